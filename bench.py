@@ -1,0 +1,366 @@
+"""Benchmark of the AxLocal hot path on GB300 (one JSON line on rank 0).
+
+Workload (the order sweep at its headline order): perturbed trilinear box of
+64 x 64 x 32 = 131072 elements at N = 7 (67.1M local DOFs), X ~ U(-1, 1)
+float64.  One step = one AxLocal over the whole mesh (all steps of the hot
+path: geometry, forward contractions, geometric product, transposed
+contractions) in the FP64-accurate trilinear-recompute kernel.  Inputs
+(1.07 GB per step) are larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep]
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload
+(weak scaling, no collective on the data path); value = all ranks' DOFs /
+max-over-ranks time.  The reference arm (--impl reference) times the FP64
+CPU oracle on the host cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AxLocal GDOF/s & % roofline vs N (recompute vs stored G); PCG time-to-1e-8"
+UNIT = "GDOF/s"
+HEADLINE_N = 7
+HEADLINE_KIND = "trilinear"
+HEADLINE_PREC = "f64dw"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 SMSPs x 32)
+FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (measured 1.19 TFLOP/s)
+
+# dram bytes per launch from committed ncu captures, valid while the kernel
+# sources hash to the recorded value (else reported as null).
+TRAFFIC = {}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2504_07042_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        load = sorted(sm)[len(sm) // 4:] or sm  # drop the idle head of the record
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def _build_case(ax, torch, dev, N, kind, prec, mesh="trilinear", box=None):
+    from paper_2504_07042_gb300 import inputs
+    ex, ey, ez = box or inputs.sweep_box(N)
+    if mesh == "parallelepiped":
+        V = inputs.parallelepiped_vertices(ex, ey, ez)
+    else:
+        V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, prec)
+    X = torch.from_numpy(inputs.element_vectors(V.shape[0], N, seed=1)).to(dev, op.dtype)
+    Y = torch.empty_like(X)
+    return op, X, Y, V
+
+
+def _time_launches(torch, fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        fn()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps  # ms
+
+
+def _pipe_peak(info, sm_mhz):
+    clk = (sm_mhz or 1980.0) * 1e6
+    if info["pipe"] == 0:
+        return FP64_OPS_PER_SM_CLK * SM_COUNT * clk, "FP64 pipe"
+    return FP32_LANES_PER_SM * SM_COUNT * clk, "FP32 pipe"
+
+
+def _roofline(info, ms, sm_mhz, hbm_gbs):
+    """Time-based roofline of Sec. 3.4: T_mem = bytes / measured HBM bandwidth,
+    T_cmp = pipe instructions / pipe peak; frac = max(T_cmp, T_mem) / T_meas."""
+    E = info["E"]
+    t = ms * 1e-3
+    bytes_ = info["bytes_per_element"] * E
+    ops = info["pipe_ops_per_element"] * E
+    pipe_peak, pipe_name = _pipe_peak(info, sm_mhz)
+    t_mem = bytes_ / (hbm_gbs * 1e9)
+    t_cmp = ops / pipe_peak
+    F = info["flops_ax_per_element"] * E
+    r = {
+        "t_mem_ms": t_mem * 1e3, "t_cmp_ms": t_cmp * 1e3, "t_meas_ms": ms,
+        "P_eff_gflops": F / t / 1e9, "R_eff_gflops": F / max(t_mem, t_cmp) / 1e9,
+        "frac_time_roofline": max(t_mem, t_cmp) / t,
+        "hbm_gbs_achieved": bytes_ / t / 1e9, "pipe": pipe_name,
+    }
+    if t_cmp >= t_mem:
+        r.update({"bound": "alu", "achieved": ops / t / 1e12, "peak": pipe_peak / 1e12,
+                  "unit": "Tinst/s (%s lane-instructions)" % pipe_name})
+    else:
+        r.update({"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm_gbs, "unit": "GB/s"})
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_oracle_rate(seconds=10.0, N=HEADLINE_N):
+    """FP64 oracle AxLocal (Eq. 9 + Eq. 7 + Algorithm 1, OpenMP over elements)
+    on a bounded sample of the workload mesh; returns (GDOF/s, cores, sample)."""
+    from oracle import oracle
+    from paper_2504_07042_gb300 import inputs
+    ex, ey, ez = inputs.sweep_box(N)
+    V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    n3 = (N + 1) ** 3
+    pilot = 512
+    X = inputs.element_vectors(pilot, N, seed=1)
+    t = time.perf_counter()
+    oracle.axlocal_vertices(V[:pilot], X, N)
+    dt = time.perf_counter() - t
+    m = int(min(V.shape[0], max(pilot, pilot * seconds / max(dt, 1e-6))))
+    X = inputs.element_vectors(m, N, seed=1)
+    reps, t = 0, time.perf_counter()
+    while True:  # whole passes over the sample until about `seconds` of CPU work
+        oracle.axlocal_vertices(V[:m], X, N)
+        reps += 1
+        dt = time.perf_counter() - t
+        if dt >= seconds:
+            break
+    return (reps * m * n3 / dt / 1e9, oracle.num_threads(),
+            "%d pass(es) over the first %d of %d elements (%.1f s)" % (reps, m, V.shape[0], dt))
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_2504_07042_gb300 import inputs
+    N = HEADLINE_N
+    ex, ey, ez = inputs.sweep_box(N)
+    V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    n3 = (N + 1) ** 3
+    m = 2048  # elements per step: a bounded sample of the workload
+    X = inputs.element_vectors(m, N, seed=1)
+    for _ in range(args.warmup):
+        oracle.axlocal_vertices(V[:m], X, N)
+    t = time.perf_counter()
+    for s in range(args.steps):
+        lo = (s * m) % (V.shape[0] - m)
+        oracle.axlocal_vertices(V[lo:lo + m], X, N)
+    dt = (time.perf_counter() - t) / args.steps
+    val = m * n3 / dt / 1e9
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "order-7 sweep mesh 64x64x32 perturbed trilinear, %d-element sample per step" % m,
+                       "kind": HEADLINE_KIND},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d elements per step of the 131072-element mesh" % m},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2504_07042_gb300 import ax
+    peaks, peak_src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    op, X, Y, V = _build_case(ax, torch, dev, HEADLINE_N, HEADLINE_KIND, HEADLINE_PREC)
+    info = op.ax_query()
+    stream = torch.cuda.current_stream()
+    E, n3 = op.E, op.n3
+    fn = lambda: op.ax_local(X, Y, stream)  # noqa: E731
+    for _ in range(max(args.warmup, 3)):
+        fn()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    with Clocks(local) as ck:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    clocks = ck.summary()
+    value = world * E * n3 / (ms * 1e-3) / 1e9
+    roof = _roofline(info, ms, clocks.get("sm_mhz"), hbm)
+    src = _src_hash()
+    kname = "ax_dw_kernel<8,%d>" % info["kind"]
+    traffic = TRAFFIC.get(kname)
+    roof_line = {"bound": roof["bound"], "achieved": roof["achieved"], "peak": roof["peak"], "unit": roof["unit"],
+                 "frac": roof["frac"], "traffic": traffic["bytes"] if traffic and traffic["src"] == src else None,
+                 "kernel": kname, "peak_source": ("%s (%d lanes/SM x %d SMs x median SM clock)"
+                                                  % (roof["pipe"], FP32_LANES_PER_SM, SM_COUNT)
+                                                  if roof["bound"] == "alu" else "hbm_gbs of MEASURED_PEAKS.json (%s)" % peak_src),
+                 "time_based": {k: roof[k] for k in ("t_mem_ms", "t_cmp_ms", "t_meas_ms", "P_eff_gflops",
+                                                     "R_eff_gflops", "frac_time_roofline", "hbm_gbs_achieved")}}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Xh = torch.from_numpy(X.cpu().numpy()).pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    for _ in range(2):
+        op.ax_local_host(Xh, Yh, stream)
+    t = time.perf_counter()
+    e2e_steps = max(2, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        op.ax_local_host(Xh, Yh, stream)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    nbytes = X.numel() * X.element_size()
+    e2e = {"value": world * E * n3 / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+    del Xh, Yh
+
+    sweep = None
+    if not args.no_sweep and rank == 0:
+        sweep = run_sweep(ax, torch, dev, hbm, clocks.get("sm_mhz"))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64dw", "data": "synthetic",
+            "config": {"workload": "order sweep at N=7: perturbed trilinear box 64x64x32 = 131072 elements, "
+                                   "67.1M local DOFs, X~U(-1,1) float64",
+                       "kind": HEADLINE_KIND, "precision": "float64 in/out, double-word FP32-pair arithmetic",
+                       "l2": "inputs larger than L2 (1.07 GB per step); no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof_line, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
+    if rank == 0:
+        rate, cores, sample = cpu_oracle_rate()
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if sweep is not None:
+            line["sweep"] = sweep
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def run_sweep(ax, torch, dev, hbm, sm_mhz):
+    """Per-N GDOF/s and roofline fraction, recompute vs stored, per precision."""
+    out = []
+    stream = torch.cuda.current_stream()
+    for N in (3, 5, 7, 9, 11, 15):
+        for mesh, kinds in (("trilinear", ("stored", "trilinear", "partial")), ("parallelepiped", ("parallelepiped",))):
+            for prec in ("fp64", "f64dw", "fp32"):
+                for kind in kinds:
+                    op, X, Y, _ = _build_case(ax, torch, dev, N, kind, prec, mesh)
+                    info = op.ax_query()
+                    ms = _time_launches(torch, lambda: op.ax_local(X, Y, stream), 5, 2, stream)
+                    roof = _roofline(info, ms, sm_mhz, hbm)
+                    out.append({"N": N, "mesh": mesh, "kind": kind, "prec": prec, "E": op.E,
+                                "gdofs": op.E * op.n3 / (ms * 1e-3) / 1e9, "ms": ms, "bound": roof["bound"],
+                                "frac": roof["frac"], "P_eff_gflops": roof["P_eff_gflops"],
+                                "hbm_gbs": roof["hbm_gbs_achieved"]})
+                    op.ax_destroy()
+                    del X, Y
+                    torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-sweep", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,135 @@
+/*
+ * ax.h -- C ABI of libax, a GB300 (sm_103a) implementation of the
+ * matrix-free Poisson element operator of high-order spectral elements
+ * ("AxLocal", CEED bake-off kernel BK5) with on-the-fly geometric factors,
+ * after Cao, Sun, Zhang, Li, "Towards a Higher Roofline for Matrix-Vector
+ * Multiplication in Matrix-Free HOSFEM" (arXiv 2504.07042).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ *  - N is the polynomial order, N1 = N+1, n3 = N1^3 nodes per element.
+ *    Supported: 1 <= N <= 15.
+ *  - Element-local vectors X, Y are [E][n3] arrays, node [i,j,k] of element e
+ *    at offset e*n3 + i + j*N1 + k*N1^2 (i fastest; Sec. 2.2, Algorithm 1).
+ *  - Vertices are [E][8][3] float64, vertex v = a + 2b + 4c at reference
+ *    corner (2a-1, 2b-1, 2c-1): the Kronecker order of the trilinear map,
+ *    Eq. 8 (this is NOT the counter-clockwise Exodus/Nek order).
+ *  - Geometric factors are [E][7][n3] float64 in the order
+ *    g00 g01 g02 g11 g12 g22 gwj, G = w_i w_j w_k |J| J^-1 J^-T and
+ *    gwj = w_i w_j w_k |J| (Eq. 7).
+ *  - Pointers named "device" must be device memory of the current CUDA
+ *    device (or managed memory); they stay owned by the caller.  The library
+ *    copies what it keeps.  "stream" is a cudaStream_t passed as void*
+ *    (NULL = legacy default stream).  Every call is asynchronous on that
+ *    stream unless stated otherwise.
+ *  - Every call returns an ax_status; on failure, ax_last_error() gives a
+ *    message.  No call aborts the process or traps the GPU.
+ */
+#ifndef AX_H
+#define AX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ax_ctx ax_ctx;
+
+typedef enum {
+  AX_OK = 0,
+  AX_EINVAL = 1,              /* bad argument (size, pointer, enum) */
+  AX_ENOMEM = 2,              /* device allocation failed */
+  AX_ECUDA = 3,               /* a CUDA runtime call failed */
+  AX_EINVERTED = 4,           /* det J <= 0 at some GLL node */
+  AX_ENOTPARALLELEPIPED = 5,  /* AX_GEOM_PARALLELEPIPED given a non-affine element */
+  AX_ENOTCONV = 6,            /* iterative solve hit its iteration cap */
+  AX_ETIMEOUT = 7,            /* a bounded device wait gave up */
+  AX_EUNSUPPORTED = 8,        /* valid but not implemented combination */
+  AX_ERANGE = 9               /* input magnitude outside the kernel's number range */
+} ax_status;
+
+/* How the geometric factors reach the kernel (Table 3 of the paper). */
+typedef enum {
+  AX_GEOM_STORED = 0,            /* 6 of the 7 factors per node streamed from HBM ("full access") */
+  AX_GEOM_TRILINEAR = 1,         /* recomputed per node from the 8 vertices (Algorithm 2) */
+  AX_GEOM_PARALLELEPIPED = 2,    /* recomputed from one constant set per element (Algorithm 3) */
+  AX_GEOM_TRILINEAR_PARTIAL = 3  /* trilinear, with the per-node scalar w|J|^-1 stored (Sec. 4.2.2) */
+} ax_geom_kind;
+
+/* Number format of X, Y and of the arithmetic. */
+typedef enum {
+  AX_FP64 = 0,  /* X, Y float64; native FP64 arithmetic */
+  AX_FP32 = 1,  /* X, Y float32; FP32 arithmetic */
+  AX_TF32 = 2,  /* X, Y float32; contractions on tensor cores in TF32, FP32 accumulate */
+  AX_BF16 = 3,  /* X, Y float32; contractions on tensor cores in BF16, FP32 accumulate */
+  AX_FP16 = 4,  /* X, Y float32; contractions on tensor cores in FP16, FP32 accumulate */
+  AX_F64DW = 5  /* X, Y float64; arithmetic in double-word FP32 pairs (about 47 bits) on the
+                   FP32 pipe; same results as AX_FP64 to ~1e-13 relative max-norm */
+} ax_precision;
+
+/* Create a context for E elements of order N.
+ *   vertices: device, [E][8][3] float64 (Eq. 8 order).  Read during the call only.
+ *   kind, prec: see the enums.
+ * Computes GLL tables, the per-kind geometry record (stored factors via the
+ * discrete Jacobian of Sec. 3.2, vertex data, parallelepiped constants of
+ * Algorithm 3, or per-node w/|J| for the partial kind) and validates the
+ * mesh: AX_EINVERTED if det J <= 0 at any GLL node, AX_ENOTPARALLELEPIPED if
+ * kind is PARALLELEPIPED and an element is not affine (relative 1e-12).
+ * Synchronises the stream once (validity flag).  On success *out owns
+ * device memory until ax_destroy(). */
+ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_geom_kind kind,
+                   ax_precision prec, void *stream);
+
+/* AxLocal (Algorithm 1, Poisson: lambda0 = 1, lambda1 = 0):
+ *   Y[e] = A^(e) X[e] = D^T (w G) D X[e] for every element (unassembled).
+ *   X, Y: device, [E][n3], float64 for AX_FP64/AX_F64DW, float32 otherwise.
+ *   Y is overwritten; X and Y must not overlap.  One kernel launch. */
+ax_status ax_local(ax_ctx *c, const void *X, void *Y, void *stream);
+
+/* Same as ax_local with host buffers (pageable or pinned): copies X to the
+ * device, runs ax_local, copies Y back and synchronises the stream.  Uses
+ * library-owned device buffers allocated at the first call. */
+ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *stream);
+
+/* The geometric factors as the kernel of this context obtains them, written
+ * to G_out: device, [E][7][n3] float64.  Stored kinds copy their table; the
+ * recompute kinds run their in-kernel geometry code (Algorithm 2 or 3) and
+ * write its results.  For testing the geometry step on its own. */
+ax_status ax_factors(ax_ctx *c, double *G_out, void *stream);
+
+/* Physical coordinates of every node (Eq. 8 at the GLL points):
+ * XYZ_out: device, [E][3][n3] float64. */
+ax_status ax_node_coords(ax_ctx *c, double *XYZ_out, void *stream);
+
+/* Algorithmic cost of one ax_local call (per element): bytes moved to and
+ * from HBM by the kernel's design, the paper's effective flops
+ * F_ax = 12 N1^4 + 15 N1^3 (Table 2), and the arithmetic instructions the
+ * kernel issues per element on its binding pipe (FP64 or FP32 lanes). */
+typedef struct {
+  int64_t E;
+  int N;
+  int kind;
+  int prec;
+  double bytes_per_element;
+  double flops_ax_per_element;
+  double pipe_ops_per_element;
+  int pipe;  /* 0 = FP64 pipe, 1 = FP32 pipe, 2 = tensor pipe */
+} ax_info;
+ax_status ax_query(const ax_ctx *c, ax_info *info);
+
+/* Message for the last failed call on this context (or on context creation
+ * when c is NULL).  Owned by the library; valid until the next call. */
+const char *ax_last_error(const ax_ctx *c);
+
+/* Name of a status code. */
+const char *ax_status_string(ax_status s);
+
+/* Release everything the context owns.  NULL is accepted. */
+void ax_destroy(ax_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AX_H */

@@ -1,0 +1,143 @@
+"""Thin ctypes binding of libax (include/ax.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Tensors are torch CUDA tensors (device memory and streams are the
+only things PyTorch provides); host buffers for ``ax_local_host`` are numpy
+arrays or CPU tensors.  If libax.so has not been built, importing this module
+raises ``ImportError`` -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libax.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libax.so is not built (run paper_2504_07042_gb300.build.build()); no fallback exists")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# enums (mirror include/ax.h)
+AX_OK, AX_EINVAL, AX_ENOMEM, AX_ECUDA, AX_EINVERTED, AX_ENOTPARALLELEPIPED, AX_ENOTCONV, AX_ETIMEOUT, \
+    AX_EUNSUPPORTED, AX_ERANGE = range(10)
+AX_GEOM_STORED, AX_GEOM_TRILINEAR, AX_GEOM_PARALLELEPIPED, AX_GEOM_TRILINEAR_PARTIAL = range(4)
+AX_FP64, AX_FP32, AX_TF32, AX_BF16, AX_FP16, AX_F64DW = range(6)
+
+KINDS = {"stored": AX_GEOM_STORED, "trilinear": AX_GEOM_TRILINEAR, "parallelepiped": AX_GEOM_PARALLELEPIPED,
+         "partial": AX_GEOM_TRILINEAR_PARTIAL}
+PRECS = {"fp64": AX_FP64, "fp32": AX_FP32, "tf32": AX_TF32, "bf16": AX_BF16, "fp16": AX_FP16, "f64dw": AX_F64DW}
+
+
+class ax_info(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_int64), ("N", ctypes.c_int), ("kind", ctypes.c_int), ("prec", ctypes.c_int),
+                ("bytes_per_element", ctypes.c_double), ("flops_ax_per_element", ctypes.c_double),
+                ("pipe_ops_per_element", ctypes.c_double), ("pipe", ctypes.c_int)]
+
+
+_vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+_lib.ax_setup.argtypes = [ctypes.POINTER(_vp), _i64, _int, _vp, _int, _int, _vp]
+_lib.ax_setup.restype = _int
+_lib.ax_local.argtypes = [_vp, _vp, _vp, _vp]
+_lib.ax_local.restype = _int
+_lib.ax_local_host.argtypes = [_vp, _vp, _vp, _vp]
+_lib.ax_local_host.restype = _int
+_lib.ax_factors.argtypes = [_vp, _vp, _vp]
+_lib.ax_factors.restype = _int
+_lib.ax_node_coords.argtypes = [_vp, _vp, _vp]
+_lib.ax_node_coords.restype = _int
+_lib.ax_query.argtypes = [_vp, ctypes.POINTER(ax_info)]
+_lib.ax_query.restype = _int
+_lib.ax_last_error.argtypes = [_vp]
+_lib.ax_last_error.restype = ctypes.c_char_p
+_lib.ax_status_string.argtypes = [_int]
+_lib.ax_status_string.restype = ctypes.c_char_p
+_lib.ax_destroy.argtypes = [_vp]
+_lib.ax_destroy.restype = None
+
+EXPORTS = ("ax_setup", "ax_local", "ax_local_host", "ax_factors", "ax_node_coords", "ax_query",
+           "ax_last_error", "ax_status_string", "ax_destroy")
+
+
+class AxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_lib.ax_status_string(status).decode(), msg))
+        self.status = status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):  # numpy
+        return t.ctypes.data
+    return int(t)
+
+
+def _check(st: int, ctx=None):
+    if st != AX_OK:
+        raise AxError(st, _lib.ax_last_error(ctx).decode())
+
+
+class Ax:
+    """Owns an ax_ctx.  Method names follow the C ABI."""
+
+    def __init__(self, vertices, N: int, kind="trilinear", prec="fp64", stream=None):
+        import torch
+        kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+        if not (isinstance(vertices, torch.Tensor) and vertices.is_cuda and vertices.dtype == torch.float64):
+            raise TypeError("vertices must be a float64 CUDA tensor [E][8][3]")
+        vertices = vertices.contiguous()
+        self.E = int(vertices.shape[0])
+        self.N = int(N)
+        self.kind, self.prec = kind, prec
+        self.ctx = _vp()
+        _check(_lib.ax_setup(ctypes.byref(self.ctx), self.E, self.N, _ptr(vertices), kind, prec, _stream(stream)))
+        self.n3 = (self.N + 1) ** 3
+        self.dtype = torch.float64 if prec in (AX_FP64, AX_F64DW) else torch.float32
+
+    def ax_local(self, X, Y, stream=None):
+        _check(_lib.ax_local(self.ctx, _ptr(X), _ptr(Y), _stream(stream)), self.ctx)
+        return Y
+
+    def ax_local_host(self, X_host, Y_host, stream=None):
+        _check(_lib.ax_local_host(self.ctx, _ptr(X_host), _ptr(Y_host), _stream(stream)), self.ctx)
+        return Y_host
+
+    def ax_factors(self, G_out, stream=None):
+        _check(_lib.ax_factors(self.ctx, _ptr(G_out), _stream(stream)), self.ctx)
+        return G_out
+
+    def ax_node_coords(self, XYZ_out, stream=None):
+        _check(_lib.ax_node_coords(self.ctx, _ptr(XYZ_out), _stream(stream)), self.ctx)
+        return XYZ_out
+
+    def ax_query(self) -> dict:
+        info = ax_info()
+        _check(_lib.ax_query(self.ctx, ctypes.byref(info)), self.ctx)
+        return {k: getattr(info, k) for k, _ in ax_info._fields_}
+
+    def ax_destroy(self):
+        if self.ctx:
+            _lib.ax_destroy(self.ctx)
+            self.ctx = _vp()
+
+    def __del__(self):
+        try:
+            self.ax_destroy()
+        except Exception:
+            pass
+
+
+def ax_setup(vertices, N, kind="trilinear", prec="fp64", stream=None) -> Ax:
+    return Ax(vertices, N, kind, prec, stream)

@@ -1,0 +1,299 @@
+// C-ABI layer of libax (include/ax.h): argument checks, context ownership,
+// dispatch to the kernel translation units, status and error strings.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ax_internal.h"
+
+struct ax_ctx {
+  ax::Ctx c;
+  double *vtx = nullptr;  // copy of the caller's vertices (node coordinates, exports)
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+ax_status fail(ax_ctx *c, ax_status st, const std::string &msg) {
+  if (c)
+    c->c.err = msg;
+  else
+    g_create_err = msg;
+  return st;
+}
+
+ax_status cuda_fail(ax_ctx *c, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  (void)cudaGetLastError();  // clear a sticky launch error where possible
+  return fail(c, e == cudaErrorMemoryAllocation ? AX_ENOMEM : AX_ECUDA, m);
+}
+
+bool is_f64_io(ax_precision p) { return p == AX_FP64 || p == AX_F64DW; }
+
+size_t storage_word(ax_precision p) {
+  // bytes per geometry value: float64, double-word pair, or float32
+  return (p == AX_FP64 || p == AX_F64DW) ? 8 : 4;
+}
+
+size_t io_word(ax_precision p) { return is_f64_io(p) ? 8 : 4; }
+
+void release(ax_ctx *c) {
+  if (!c) return;
+  cudaFree(c->c.geo);
+  cudaFree(c->c.lam);
+  cudaFree(c->c.hx);
+  cudaFree(c->c.hy);
+  cudaFree(c->vtx);
+  c->c.geo = c->c.lam = c->c.hx = c->c.hy = nullptr;
+  c->vtx = nullptr;
+}
+
+ax::AxArgs make_args(ax_ctx *c, const void *X, void *Y, void *stream) {
+  ax::AxArgs a;
+  a.E = c->c.E;
+  a.N = c->c.N;
+  a.kind = c->c.kind;
+  a.geo = c->c.geo;
+  a.lam = c->c.lam;
+  a.X = X;
+  a.Y = Y;
+  a.stream = (cudaStream_t)stream;
+  return a;
+}
+
+cudaError_t run_ax(ax_ctx *c, const ax::AxArgs &a) {
+  switch (c->c.prec) {
+    case AX_FP64: return ax::launch_ax_fp64(a);
+    case AX_FP32: return ax::launch_ax_fp32(a);
+    case AX_F64DW: return ax::launch_ax_dw(a);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+bool same_device(ax_ctx *c) {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == c->c.device;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ax_status_string(ax_status s) {
+  switch (s) {
+    case AX_OK: return "AX_OK";
+    case AX_EINVAL: return "AX_EINVAL";
+    case AX_ENOMEM: return "AX_ENOMEM";
+    case AX_ECUDA: return "AX_ECUDA";
+    case AX_EINVERTED: return "AX_EINVERTED";
+    case AX_ENOTPARALLELEPIPED: return "AX_ENOTPARALLELEPIPED";
+    case AX_ENOTCONV: return "AX_ENOTCONV";
+    case AX_ETIMEOUT: return "AX_ETIMEOUT";
+    case AX_EUNSUPPORTED: return "AX_EUNSUPPORTED";
+    case AX_ERANGE: return "AX_ERANGE";
+  }
+  return "AX_UNKNOWN";
+}
+
+const char *ax_last_error(const ax_ctx *c) { return c ? c->c.err.c_str() : g_create_err.c_str(); }
+
+ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_geom_kind kind, ax_precision prec,
+                   void *stream) {
+  if (!out) return fail(nullptr, AX_EINVAL, "ax_setup: out is NULL");
+  *out = nullptr;
+  if (E < 0) return fail(nullptr, AX_EINVAL, "ax_setup: E < 0");
+  if (N < 1 || N > ax::kMaxN) return fail(nullptr, AX_EINVAL, "ax_setup: N must be in [1, 15]");
+  if (E > 0 && !vertices) return fail(nullptr, AX_EINVAL, "ax_setup: vertices is NULL");
+  if ((int)kind < 0 || (int)kind > 3) return fail(nullptr, AX_EINVAL, "ax_setup: bad geometry kind");
+  if ((int)prec < 0 || (int)prec > 5) return fail(nullptr, AX_EINVAL, "ax_setup: bad precision");
+  if (prec == AX_TF32 || prec == AX_BF16 || prec == AX_FP16)
+    return fail(nullptr, AX_EUNSUPPORTED, "ax_setup: tensor-core precisions are not available in AxLocal contexts");
+  const int64_t N1 = N + 1, n3 = N1 * N1 * N1;
+  if (E > (int64_t)1 << 40 || E * n3 > ((int64_t)1 << 46))
+    return fail(nullptr, AX_EINVAL, "ax_setup: problem too large");
+
+  ax_ctx *c = new (std::nothrow) ax_ctx;
+  if (!c) return fail(nullptr, AX_ENOMEM, "ax_setup: host allocation failed");
+  c->c.E = E;
+  c->c.N = N;
+  c->c.N1 = (int)N1;
+  c->c.n3 = (int)n3;
+  c->c.kind = kind;
+  c->c.prec = prec;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->c.device);
+  if (e == cudaSuccess) e = ax::upload_tables_setup(c->c.device);
+  if (e == cudaSuccess) {
+    switch (prec) {
+      case AX_FP64: e = ax::upload_tables_fp64(c->c.device); break;
+      case AX_FP32: e = ax::upload_tables_fp32(c->c.device); break;
+      case AX_F64DW: e = ax::upload_tables_dw(c->c.device); break;
+      default: break;
+    }
+  }
+  if (e != cudaSuccess) {
+    ax_status st = cuda_fail(nullptr, e, "ax_setup: table upload");
+    delete c;
+    return st;
+  }
+  const size_t gw = storage_word(prec);
+  size_t geo_words = 0;
+  switch (kind) {
+    case AX_GEOM_STORED: geo_words = (size_t)E * 7 * n3; break;
+    case AX_GEOM_PARALLELEPIPED: geo_words = (size_t)E * ax::kParWords; break;
+    default: geo_words = (size_t)E * ax::kVertexWords; break;
+  }
+  c->c.geo_bytes = geo_words * gw;
+  c->c.lam_bytes = kind == AX_GEOM_TRILINEAR_PARTIAL ? (size_t)E * n3 * gw : 0;
+  int *flags = nullptr;
+  if (E > 0) {
+    e = cudaMalloc(&c->c.geo, c->c.geo_bytes);
+    if (e == cudaSuccess && c->c.lam_bytes) e = cudaMalloc(&c->c.lam, c->c.lam_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->vtx, (size_t)E * 24 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->vtx, vertices, (size_t)E * 24 * sizeof(double), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);
+    if (e == cudaSuccess) e = ax::setup_geometry(c->c, c->vtx, c->c.geo, c->c.lam, flags, s);
+    int hflags[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flags);
+    if (e != cudaSuccess) {
+      ax_status st = cuda_fail(nullptr, e, "ax_setup");
+      release(c);
+      delete c;
+      return st;
+    }
+    ax_status st = AX_OK;
+    char msg[160];
+    if (hflags[0]) {
+      snprintf(msg, sizeof msg, "ax_setup: det J <= 0 at %d GLL nodes", hflags[0]);
+      st = fail(nullptr, AX_EINVERTED, msg);
+    } else if (kind == AX_GEOM_PARALLELEPIPED && hflags[1]) {
+      snprintf(msg, sizeof msg, "ax_setup: %d elements are not parallelepipeds", hflags[1]);
+      st = fail(nullptr, AX_ENOTPARALLELEPIPED, msg);
+    } else if (hflags[2]) {
+      snprintf(msg, sizeof msg, "ax_setup: %d geometry values above 1e30 (or not finite) for an FP32-based precision", hflags[2]);
+      st = fail(nullptr, AX_ERANGE, msg);
+    }
+    if (st != AX_OK) {
+      release(c);
+      delete c;
+      return st;
+    }
+  }
+  *out = c;
+  return AX_OK;
+}
+
+ax_status ax_local(ax_ctx *c, const void *X, void *Y, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_local: context is NULL");
+  if (c->c.E == 0) return AX_OK;
+  if (!X || !Y) return fail(c, AX_EINVAL, "ax_local: X or Y is NULL");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_local: current device differs from the context's");
+  const size_t bytes = (size_t)c->c.E * c->c.n3 * io_word(c->c.prec);
+  const char *x = (const char *)X, *y = (const char *)Y;
+  if (x < y + bytes && y < x + bytes) return fail(c, AX_EINVAL, "ax_local: X and Y overlap");
+  cudaError_t e = run_ax(c, make_args(c, X, Y, stream));
+  if (e == cudaErrorNotSupported) return fail(c, AX_EUNSUPPORTED, "ax_local: precision not supported");
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_local launch");
+  return AX_OK;
+}
+
+ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_local_host: context is NULL");
+  if (c->c.E == 0) return AX_OK;
+  if (!X_host || !Y_host) return fail(c, AX_EINVAL, "ax_local_host: X or Y is NULL");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_local_host: current device differs from the context's");
+  const size_t bytes = (size_t)c->c.E * c->c.n3 * io_word(c->c.prec);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (c->c.hbytes < bytes) {
+    cudaFree(c->c.hx);
+    cudaFree(c->c.hy);
+    c->c.hx = c->c.hy = nullptr;
+    c->c.hbytes = 0;
+    e = cudaMalloc(&c->c.hx, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->c.hy, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host: staging allocation");
+    c->c.hbytes = bytes;
+  }
+  e = cudaMemcpyAsync(c->c.hx, X_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = run_ax(c, make_args(c, c->c.hx, c->c.hy, stream));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Y_host, c->c.hy, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host");
+  return AX_OK;
+}
+
+ax_status ax_factors(ax_ctx *c, double *G_out, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_factors: context is NULL");
+  if (c->c.E == 0) return AX_OK;
+  if (!G_out) return fail(c, AX_EINVAL, "ax_factors: G_out is NULL");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_factors: current device differs from the context's");
+  ax::AxArgs a = make_args(c, nullptr, nullptr, stream);
+  cudaError_t e;
+  switch (c->c.prec) {
+    case AX_FP64: e = ax::launch_factors_fp64(a, G_out); break;
+    case AX_FP32: e = ax::launch_factors_fp32(a, G_out); break;
+    case AX_F64DW: e = ax::launch_factors_dw(a, G_out); break;
+    default: return fail(c, AX_EUNSUPPORTED, "ax_factors: precision not supported");
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_factors launch");
+  return AX_OK;
+}
+
+ax_status ax_node_coords(ax_ctx *c, double *XYZ_out, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_node_coords: context is NULL");
+  if (c->c.E == 0) return AX_OK;
+  if (!XYZ_out) return fail(c, AX_EINVAL, "ax_node_coords: XYZ_out is NULL");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_node_coords: current device differs from the context's");
+  cudaError_t e = ax::setup_node_coords(c->c, c->vtx, XYZ_out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_node_coords launch");
+  return AX_OK;
+}
+
+ax_status ax_query(const ax_ctx *c, ax_info *info) {
+  if (!c || !info) return AX_EINVAL;
+  const double N1 = c->c.N1, n3 = c->c.n3;
+  const double io = (double)io_word(c->c.prec), gw = (double)storage_word(c->c.prec);
+  info->E = c->c.E;
+  info->N = c->c.N;
+  info->kind = (int)c->c.kind;
+  info->prec = (int)c->c.prec;
+  double geo_bytes = 0.0;
+  switch (c->c.kind) {
+    case AX_GEOM_STORED: geo_bytes = 6.0 * n3 * gw; break;  // the Poisson kernel reads 6 of 7
+    case AX_GEOM_PARALLELEPIPED: geo_bytes = ax::kParWords * gw; break;
+    case AX_GEOM_TRILINEAR: geo_bytes = ax::kVertexWords * gw; break;
+    case AX_GEOM_TRILINEAR_PARTIAL: geo_bytes = (ax::kVertexWords + n3) * gw; break;
+  }
+  info->bytes_per_element = 2.0 * n3 * io + geo_bytes;
+  info->flops_ax_per_element = 12.0 * N1 * N1 * N1 * N1 + 15.0 * n3;
+  // arithmetic instructions per node on the binding pipe (design counts):
+  // contractions 6*N1, geometric product 9, geometry by kind.
+  double geo_ops = 0.0;
+  switch (c->c.kind) {
+    case AX_GEOM_STORED: geo_ops = 0.0; break;
+    case AX_GEOM_PARALLELEPIPED: geo_ops = 7.0; break;
+    case AX_GEOM_TRILINEAR: geo_ops = 6 + 15 + 12 + 9 + 1 + 6 + 8; break;  // cols, K, adj, det, W, scale, division
+    case AX_GEOM_TRILINEAR_PARTIAL: geo_ops = 6 + 15 + 12 + 6; break;
+  }
+  double per_node = 6.0 * N1 + 9.0 + geo_ops;
+  info->pipe = (c->c.prec == AX_FP64) ? 0 : 1;
+  if (c->c.prec == AX_F64DW) per_node = ax::dw_ops_per_node(c->c.N1, (int)c->c.kind);
+  info->pipe_ops_per_element = per_node * n3;
+  return AX_OK;
+}
+
+void ax_destroy(ax_ctx *c) {
+  if (!c) return;
+  release(c);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,4 @@
+// AxLocal kernels, double-word arithmetic, orders N = 6, 7.
+#define AX_TAG dw_g1
+#define AX_N_LIST(X) X(6) X(7)
+#include "inst_dw.inc"

@@ -1,0 +1,5 @@
+// AxLocal kernels, native FP32 arithmetic, orders N = 10, 11.
+#define AX_T float
+#define AX_TAG fp32_g3
+#define AX_N_LIST(X) X(10) X(11)
+#include "inst_native.inc"

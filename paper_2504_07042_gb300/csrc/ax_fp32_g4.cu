@@ -1,0 +1,5 @@
+// AxLocal kernels, native FP32 arithmetic, orders N = 12, 13.
+#define AX_T float
+#define AX_TAG fp32_g4
+#define AX_N_LIST(X) X(12) X(13)
+#include "inst_native.inc"

@@ -1,0 +1,5 @@
+// AxLocal kernels, native FP64 arithmetic, orders N = 8, 9.
+#define AX_T double
+#define AX_TAG fp64_g2
+#define AX_N_LIST(X) X(8) X(9)
+#include "inst_native.inc"

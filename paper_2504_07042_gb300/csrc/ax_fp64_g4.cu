@@ -1,0 +1,5 @@
+// AxLocal kernels, native FP64 arithmetic, orders N = 12, 13.
+#define AX_T double
+#define AX_TAG fp64_g4
+#define AX_N_LIST(X) X(12) X(13)
+#include "inst_native.inc"

@@ -1,0 +1,5 @@
+// AxLocal kernels, native FP64 arithmetic, orders N = 15.
+#define AX_T double
+#define AX_TAG fp64_g6
+#define AX_N_LIST(X) X(15)
+#include "inst_native.inc"

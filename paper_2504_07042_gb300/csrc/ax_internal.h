@@ -1,0 +1,83 @@
+// Internal declarations shared by the C-ABI layer (ax_api.cu) and the kernel
+// translation units.  Not installed; the public interface is include/ax.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/ax.h"
+#include "gll.h"
+
+namespace ax {
+
+// Per-element geometry record sizes (words of the storage type).
+constexpr int kVertexWords = 24;  // 8 vertices x 3, relative to vertex 0 (row 0 is zero)
+constexpr int kParWords = 8;      // h0..h6 of Algorithm 3 + one pad word
+
+// Device tables for one polynomial order, uploaded once per device by each
+// kernel translation unit into its own constant memory.
+struct GllHost {
+  int N = 0;
+  double x[kMaxN1], w[kMaxN1], D[kMaxN1 * kMaxN1];
+};
+
+struct Ctx {
+  int64_t E = 0;
+  int N = 0, N1 = 0, n3 = 0;
+  ax_geom_kind kind = AX_GEOM_STORED;
+  ax_precision prec = AX_FP64;
+  int device = 0;
+  // geometry record, in the storage type of the precision:
+  //   STORED: factors [E][7][n3]; TRILINEAR(_PARTIAL): vertices [E][24];
+  //   PARALLELEPIPED: constants [E][8]; PARTIAL additionally lam [E][n3].
+  void *geo = nullptr;
+  size_t geo_bytes = 0;
+  void *lam = nullptr;
+  size_t lam_bytes = 0;
+  // device staging buffers for ax_local_host
+  void *hx = nullptr, *hy = nullptr;
+  size_t hbytes = 0;
+  std::string err;
+};
+
+// Argument bundle handed to every AxLocal launcher.
+struct AxArgs {
+  int64_t E;
+  int N;
+  ax_geom_kind kind;
+  const void *geo;
+  const void *lam;
+  const void *X;
+  void *Y;
+  cudaStream_t stream;
+};
+
+// Launchers (return cudaSuccess or the launch error).
+cudaError_t launch_ax_fp64(const AxArgs &a);
+cudaError_t launch_ax_fp32(const AxArgs &a);
+cudaError_t launch_ax_dw(const AxArgs &a);
+
+// Factor export through the kernel's own geometry code (G_out [E][7][n3] float64).
+cudaError_t launch_factors_fp64(const AxArgs &a, double *G_out);
+cudaError_t launch_factors_fp32(const AxArgs &a, double *G_out);
+cudaError_t launch_factors_dw(const AxArgs &a, double *G_out);
+
+// Per-device table upload of each translation unit (idempotent per device).
+cudaError_t upload_tables_fp64(int device);
+cudaError_t upload_tables_fp32(int device);
+cudaError_t upload_tables_dw(int device);
+cudaError_t upload_tables_setup(int device);
+
+// FP32-pipe instructions per node of the double-word kernel (design count).
+double dw_ops_per_node(int N1, int kind);
+
+// Setup kernels (FP64, ax_setup.cu).  flags: device int[4] zeroed by the caller:
+//   [0] count of GLL nodes with det J <= 0, [1] count of non-affine elements,
+//   [2] count of values outside the precision's number range.
+cudaError_t setup_geometry(const Ctx &c, const double *vertices, void *geo, void *lam, int *flags,
+                           cudaStream_t s);
+cudaError_t setup_node_coords(const Ctx &c, const double *vertices, double *xyz, cudaStream_t s);
+
+}  // namespace ax

@@ -1,0 +1,250 @@
+// Setup-stage kernels (FP64 arithmetic; run once per context):
+//   - validation: det J > 0 at every GLL node (analytic trilinear Jacobian),
+//   - STORED: the seven factors per node from the standard discrete Jacobian
+//     of Sec. 3.2 (nodal coordinates, then the discrete gradient D of
+//     Table 1), then Eq. 7,
+//   - PARALLELEPIPED: h0..h6 of Algorithm 3 from the constant Jacobian, plus
+//     a check that every element is affine,
+//   - TRILINEAR kinds: vertex coordinates relative to vertex 0 (24 words),
+//   - PARTIAL: the per-node scalar w_i w_j w_k / det J (Sec. 4.2.2),
+//   - node coordinates (Eq. 8 at the GLL points).
+// Results are written in the storage format of the context's precision:
+// float64, float32, or a double-word pair (float hi, float lo).
+#include <cstdint>
+
+#include "ax_internal.h"
+#include "tables.cuh"
+
+namespace ax {
+namespace setup {
+
+static __constant__ double c_D[kTabD];
+static __constant__ double c_w[kTabV];
+static __constant__ double c_x[kTabV];
+
+enum Store { kF64 = 0, kF32 = 1, kDW = 2 };
+
+// Write v in the storage format.  FP32-based formats: values above 1e30 are
+// counted as out of range (products of them could overflow); values below
+// 1e-30 are stored as zero (an absolute error far below the tolerances).
+__device__ __forceinline__ void store(void *base, int64_t idx, double v, int fmt, int *flags) {
+  if (fmt == kF64) {
+    ((double *)base)[idx] = v;
+    return;
+  }
+  const double a = fabs(v);
+  if (!(a <= 1e30)) atomicAdd(&flags[2], 1);
+  if (a < 1e-30) v = 0.0;
+  if (fmt == kF32) {
+    ((float *)base)[idx] = (float)v;
+  } else {
+    const float hi = (float)v;
+    const float lo = (float)(v - (double)hi);
+    ((float2 *)base)[idx] = make_float2(hi, lo);
+  }
+}
+
+// Trilinear map (Eq. 8) at reference point (r,s,t).
+__device__ void map_point(const double *V, double r, double s, double t, double X[3]) {
+  for (int c = 0; c < 3; ++c) X[c] = 0.0;
+  for (int v = 0; v < 8; ++v) {
+    const double wv = (1.0 + ((v & 1) ? r : -r)) * (1.0 + ((v & 2) ? s : -s)) * (1.0 + ((v & 4) ? t : -t)) * 0.125;
+    for (int c = 0; c < 3; ++c) X[c] += wv * V[3 * v + c];
+  }
+}
+
+// Analytic Jacobian of the trilinear map, J[c][d] = d x_c / d ref_d.
+__device__ void map_jacobian(const double *V, double r, double s, double t, double J[9]) {
+  for (int q = 0; q < 9; ++q) J[q] = 0.0;
+  for (int v = 0; v < 8; ++v) {
+    const double sr = (v & 1) ? 1.0 : -1.0, ss = (v & 2) ? 1.0 : -1.0, st = (v & 4) ? 1.0 : -1.0;
+    const double fr = 1.0 + sr * r, fs = 1.0 + ss * s, ft = 1.0 + st * t;
+    const double d[3] = {sr * fs * ft * 0.125, fr * ss * ft * 0.125, fr * fs * st * 0.125};
+    for (int c = 0; c < 3; ++c)
+      for (int q = 0; q < 3; ++q) J[3 * c + q] += d[q] * V[3 * v + c];
+  }
+}
+
+__device__ double det3(const double J[9]) {
+  return J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+}
+
+// G = W |J| J^-1 J^-T = W adj(J) adj(J)^T / det J  (6 entries), gwj = W det J.
+__device__ void factors_from_J(const double J[9], double W, double g[7]) {
+  const double det = det3(J);
+  double A[9];  // adjugate (transpose of the cofactor matrix): J^-1 = A / det
+  A[0] = J[4] * J[8] - J[5] * J[7];
+  A[1] = J[2] * J[7] - J[1] * J[8];
+  A[2] = J[1] * J[5] - J[2] * J[4];
+  A[3] = J[5] * J[6] - J[3] * J[8];
+  A[4] = J[0] * J[8] - J[2] * J[6];
+  A[5] = J[2] * J[3] - J[0] * J[5];
+  A[6] = J[3] * J[7] - J[4] * J[6];
+  A[7] = J[1] * J[6] - J[0] * J[7];
+  A[8] = J[0] * J[4] - J[1] * J[3];
+  const int pr[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+  for (int q = 0; q < 6; ++q) {
+    const int p = pr[q][0], m = pr[q][1];
+    const double dot = A[3 * p] * A[3 * m] + A[3 * p + 1] * A[3 * m + 1] + A[3 * p + 2] * A[3 * m + 2];
+    g[q] = W * dot / det;
+  }
+  g[6] = W * det;
+}
+
+// One thread per node.  flags[0] += nodes with det J <= 0.
+__global__ void validate_kernel(int64_t E, int N1, const double *__restrict__ V, int *flags) {
+  const int64_t n3 = (int64_t)N1 * N1 * N1;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= E * n3) return;
+  const int64_t e = gidx / n3;
+  const int l = (int)(gidx % n3), i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+  const double *cx = c_x + tab_off_v(N1);
+  double J[9];
+  map_jacobian(V + 24 * e, cx[i], cx[j], cx[k], J);
+  if (!(det3(J) > 0.0)) atomicAdd(&flags[0], 1);
+}
+
+// STORED: discrete Jacobian of Sec. 3.2 -- the derivative along each reference
+// direction is D applied to the nodal coordinates on the line through the node.
+__global__ void stored_factors_kernel(int64_t E, int N1, const double *__restrict__ V, void *G, int fmt, int *flags) {
+  const int64_t n3 = (int64_t)N1 * N1 * N1;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= E * n3) return;
+  const int64_t e = gidx / n3;
+  const int l = (int)(gidx % n3), i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+  const double *cD = c_D + tab_off_D(N1), *cx = c_x + tab_off_v(N1), *cw = c_w + tab_off_v(N1);
+  const double *Ve = V + 24 * e;
+  double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int n = 0; n < N1; ++n) {
+    double Xr[3], Xs[3], Xt[3];
+    map_point(Ve, cx[n], cx[j], cx[k], Xr);
+    map_point(Ve, cx[i], cx[n], cx[k], Xs);
+    map_point(Ve, cx[i], cx[j], cx[n], Xt);
+    for (int c = 0; c < 3; ++c) {
+      J[3 * c + 0] += cD[i * N1 + n] * Xr[c];
+      J[3 * c + 1] += cD[j * N1 + n] * Xs[c];
+      J[3 * c + 2] += cD[k * N1 + n] * Xt[c];
+    }
+  }
+  double g[7];
+  factors_from_J(J, cw[i] * cw[j] * cw[k], g);
+  for (int q = 0; q < 7; ++q) store(G, (e * 7 + q) * n3 + l, g[q], fmt, flags);
+}
+
+// Vertices relative to vertex 0 (24 words per element; row 0 is zero).
+__global__ void relative_vertices_kernel(int64_t E, const double *__restrict__ V, void *out, int fmt, int *flags) {
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= E * 24) return;
+  const int64_t e = gidx / 24;
+  const int q = (int)(gidx % 24), c = q % 3;
+  store(out, gidx, V[24 * e + q] - V[24 * e + c], fmt, flags);
+}
+
+// PARALLELEPIPED: J = [v1-v0, v2-v0, v4-v0] / 2 (columns) is constant;
+// h0..h5 = |J| J^-1 J^-T, h6 = |J| (Algorithm 3 input, without GLL weights).
+// flags[1] += elements whose vertices deviate from v0 + a e1 + b e2 + c e3.
+__global__ void parallelepiped_kernel(int64_t E, const double *__restrict__ V, void *out, int fmt, int *flags) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const double *Ve = V + 24 * e;
+  double J[9], scale = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    J[3 * c + 0] = 0.5 * (Ve[3 + c] - Ve[c]);
+    J[3 * c + 1] = 0.5 * (Ve[6 + c] - Ve[c]);
+    J[3 * c + 2] = 0.5 * (Ve[12 + c] - Ve[c]);
+    for (int d = 0; d < 3; ++d) scale = fmax(scale, fabs(J[3 * c + d]));
+  }
+  double dev = 0.0;
+  for (int v = 0; v < 8; ++v) {
+    const int a = v & 1, b = (v >> 1) & 1, cc = (v >> 2) & 1;
+    for (int c = 0; c < 3; ++c) {
+      const double pred = Ve[c] + 2.0 * (a * J[3 * c] + b * J[3 * c + 1] + cc * J[3 * c + 2]);
+      dev = fmax(dev, fabs(pred - Ve[3 * v + c]));
+    }
+  }
+  if (dev > 1e-12 * scale) atomicAdd(&flags[1], 1);
+  double g[7];
+  factors_from_J(J, 1.0, g);
+  for (int q = 0; q < 7; ++q) store(out, e * kParWords + q, g[q], fmt, flags);
+  store(out, e * kParWords + 7, 0.0, fmt, flags);
+}
+
+// PARTIAL: lam = w_i w_j w_k / det J at every node.
+__global__ void partial_lam_kernel(int64_t E, int N1, const double *__restrict__ V, void *out, int fmt, int *flags) {
+  const int64_t n3 = (int64_t)N1 * N1 * N1;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= E * n3) return;
+  const int64_t e = gidx / n3;
+  const int l = (int)(gidx % n3), i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+  const double *cx = c_x + tab_off_v(N1), *cw = c_w + tab_off_v(N1);
+  double J[9];
+  map_jacobian(V + 24 * e, cx[i], cx[j], cx[k], J);
+  store(out, gidx, cw[i] * cw[j] * cw[k] / det3(J), fmt, flags);
+}
+
+__global__ void node_coords_kernel(int64_t E, int N1, const double *__restrict__ V, double *xyz) {
+  const int64_t n3 = (int64_t)N1 * N1 * N1;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= E * n3) return;
+  const int64_t e = gidx / n3;
+  const int l = (int)(gidx % n3), i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+  const double *cx = c_x + tab_off_v(N1);
+  double X[3];
+  map_point(V + 24 * e, cx[i], cx[j], cx[k], X);
+  for (int c = 0; c < 3; ++c) xyz[(e * 3 + c) * n3 + l] = X[c];
+}
+
+static unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace setup
+
+static UploadOnce g_once_setup;
+
+cudaError_t upload_tables_setup(int device) {
+  std::lock_guard<std::mutex> lock(g_once_setup.mu);
+  if (device < 64 && (g_once_setup.done >> device) & 1ull) return cudaSuccess;
+  static double D[kTabD], w[kTabV], x[kTabV];
+  if (!build_packed_tables(D, w, x)) return cudaErrorInvalidValue;
+  cudaError_t err = cudaMemcpyToSymbol(setup::c_D, D, sizeof(D));
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(setup::c_w, w, sizeof(w));
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(setup::c_x, x, sizeof(x));
+  if (err == cudaSuccess && device < 64) g_once_setup.done |= 1ull << device;
+  return err;
+}
+
+cudaError_t setup_geometry(const Ctx &c, const double *V, void *geo, void *lam, int *flags, cudaStream_t s) {
+  using namespace setup;
+  const int fmt = (c.prec == AX_FP64) ? kF64 : (c.prec == AX_F64DW ? kDW : kF32);
+  const int64_t nodes = c.E * (int64_t)c.n3;
+  const int B = 256;
+  if (c.E == 0) return cudaSuccess;
+  if ((nodes + B - 1) / B > 0x7fffffffLL) return cudaErrorInvalidValue;
+  validate_kernel<<<grid_for(nodes, B), B, 0, s>>>(c.E, c.N1, V, flags);
+  switch (c.kind) {
+    case AX_GEOM_STORED:
+      stored_factors_kernel<<<grid_for(nodes, B), B, 0, s>>>(c.E, c.N1, V, geo, fmt, flags);
+      break;
+    case AX_GEOM_PARALLELEPIPED:
+      parallelepiped_kernel<<<grid_for(c.E, B), B, 0, s>>>(c.E, V, geo, fmt, flags);
+      break;
+    case AX_GEOM_TRILINEAR_PARTIAL:
+      partial_lam_kernel<<<grid_for(nodes, B), B, 0, s>>>(c.E, c.N1, V, lam, fmt, flags);
+      relative_vertices_kernel<<<grid_for(c.E * 24, B), B, 0, s>>>(c.E, V, geo, fmt, flags);
+      break;
+    case AX_GEOM_TRILINEAR:
+      relative_vertices_kernel<<<grid_for(c.E * 24, B), B, 0, s>>>(c.E, V, geo, fmt, flags);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t setup_node_coords(const Ctx &c, const double *V, double *xyz, cudaStream_t s) {
+  const int64_t nodes = c.E * (int64_t)c.n3;
+  if (nodes == 0) return cudaSuccess;
+  setup::node_coords_kernel<<<setup::grid_for(nodes, 256), 256, 0, s>>>(c.E, c.N1, V, xyz);
+  return cudaGetLastError();
+}
+
+}  // namespace ax

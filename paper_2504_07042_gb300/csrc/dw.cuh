@@ -1,0 +1,127 @@
+// Double-word ("double-float") arithmetic on the FP32 pipe.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 47-48 significant bits.  GB300 runs FP32 FMA at 64x the FP64 rate,
+// so FP64-accurate AxLocal is cheaper in this form than in native FP64.
+//
+// Building blocks (all with round-to-nearest intrinsics, so the compiler can
+// neither contract nor reassociate them):
+//   TwoSum           Knuth, TAOCP vol. 2 (error-free a + b, 6 flops)
+//   Fast2Sum         Dekker 1971 (error-free a + b when |a| >= |b|, 3 flops)
+//   TwoProd          error-free a * b with one FMA (2 flops)
+//   DW * DW, DW + DW Joldes, Muller, Popescu, "Tight and rigorous error bounds
+//                    for basic building blocks of double-word arithmetic",
+//                    ACM TOMS 44(2), 2017 (DWTimesDW3, SloppyDWPlusDW)
+//   dot accumulator  compensated dot product of Ogita, Rump, Oishi,
+//                    "Accurate sum and dot product", SIAM J. Sci. Comput. 26,
+//                    2005 (Dot2), extended with the lo-part cross terms
+//   DW / DW          the same paper's DW division (DWDivDW2) with a
+//                    correctly rounded FP32 reciprocal as the seed.
+// Errors are absolute, of order 2^-47 times the magnitudes involved, which is
+// what a relative max-norm tolerance needs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ax {
+namespace dw {
+
+struct dw {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dw make(float h, float l) { return dw{h, l}; }
+__device__ __forceinline__ dw from_float2(float2 v) { return dw{v.x, v.y}; }
+
+__device__ __forceinline__ dw two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dw{s, e};
+}
+
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return dw{s, e};
+}
+
+__device__ __forceinline__ dw add(dw x, dw y) {
+  const dw s = two_sum(x.hi, y.hi);
+  const float v = __fadd_rn(x.lo, y.lo);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, v));
+}
+
+__device__ __forceinline__ dw neg(dw x) { return dw{-x.hi, -x.lo}; }
+__device__ __forceinline__ dw sub(dw x, dw y) { return add(x, neg(y)); }
+
+__device__ __forceinline__ dw mul(dw x, dw y) {
+  const float ch = __fmul_rn(x.hi, y.hi);
+  const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+  const float tl0 = __fmul_rn(x.lo, y.lo);
+  const float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+  const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+  return fast_two_sum(ch, __fadd_rn(cl1, cl2));
+}
+
+// Unnormalised dot-product accumulator: value = s + c.
+struct acc {
+  float s, c;
+};
+
+__device__ __forceinline__ acc acc_zero() { return acc{0.0f, 0.0f}; }
+
+// a += x * y  (x, y double-word)
+__device__ __forceinline__ void mac(acc &a, dw x, dw y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float pe = __fmaf_rn(x.hi, y.hi, -p);
+  const dw t = two_sum(a.s, p);
+  a.s = t.hi;
+  float c = __fadd_rn(a.c, __fadd_rn(t.lo, pe));
+  c = __fmaf_rn(x.hi, y.lo, c);
+  a.c = __fmaf_rn(x.lo, y.hi, c);
+}
+
+// first term of a fresh accumulator: a = x * y
+__device__ __forceinline__ acc mul_acc(dw x, dw y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float c = __fmaf_rn(x.hi, y.hi, -p);
+  c = __fmaf_rn(x.hi, y.lo, c);
+  c = __fmaf_rn(x.lo, y.hi, c);
+  return acc{p, c};
+}
+
+__device__ __forceinline__ void acc_add(acc &a, acc b) {
+  const dw t = two_sum(a.s, b.s);
+  a.s = t.hi;
+  a.c = __fadd_rn(__fadd_rn(a.c, b.c), t.lo);
+}
+
+__device__ __forceinline__ dw fin(acc a) { return fast_two_sum(a.s, a.c); }
+
+// x / y (DW by DW): q0 = x.hi * rcp(y.hi); r = x - q0*y (exact hi part via
+// TwoProd); q = q0 + r.hi * rcp(y.hi).
+__device__ __forceinline__ dw div(dw x, dw y) {
+  const float inv = __frcp_rn(y.hi);
+  const float q0 = __fmul_rn(x.hi, inv);
+  const float p = __fmul_rn(q0, y.hi);
+  const float pe = __fmaf_rn(q0, y.hi, -p);
+  // r = (x.hi - p) - pe + x.lo - q0 * y.lo
+  float r = __fsub_rn(x.hi, p);
+  r = __fsub_rn(r, pe);
+  r = __fadd_rn(r, x.lo);
+  r = __fmaf_rn(-q0, y.lo, r);
+  return fast_two_sum(q0, __fmul_rn(r, inv));
+}
+
+// float64 <-> double-word conversions (FP64-pipe instructions: used only at
+// the boundary of a kernel).
+__device__ __forceinline__ dw from_double(double v) {
+  const float h = __double2float_rn(v);
+  const float l = __double2float_rn(v - (double)h);
+  return dw{h, l};
+}
+__device__ __forceinline__ double to_double(dw v) { return (double)v.hi + (double)v.lo; }
+
+}  // namespace dw
+}  // namespace ax

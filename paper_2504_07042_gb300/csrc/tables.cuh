@@ -1,0 +1,42 @@
+// Per-translation-unit constant-memory copies of the GLL tables (Table 1)
+// for every supported order, so that contexts of different N can coexist.
+// Each .cu file that includes this header gets its own copy (internal
+// linkage) and uploads it once per device through upload_tables<T>().
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "gll.h"
+
+namespace ax {
+
+// Offsets of order N1 (2..16) inside the packed tables.
+__host__ __device__ constexpr int tab_off_D(int N1) { return (N1 - 1) * N1 * (2 * N1 - 1) / 6 - 1; }  // sum_{m=2}^{N1-1} m^2
+__host__ __device__ constexpr int tab_off_v(int N1) { return (N1 - 1) * N1 / 2 - 1; }                 // sum_{m=2}^{N1-1} m
+constexpr int kTabD = tab_off_D(kMaxN1 + 1);
+constexpr int kTabV = tab_off_v(kMaxN1 + 1);
+
+// Fill packed host tables (double) for all orders 1..kMaxN.
+inline bool build_packed_tables(double *D, double *w, double *x) {
+  for (int N = 1; N <= kMaxN; ++N) {
+    const int N1 = N + 1;
+    double xx[kMaxN1], ww[kMaxN1], DD[kMaxN1 * kMaxN1];
+    if (!gll_tables(N, xx, ww, DD)) return false;
+    for (int q = 0; q < N1 * N1; ++q) D[tab_off_D(N1) + q] = DD[q];
+    for (int q = 0; q < N1; ++q) {
+      w[tab_off_v(N1) + q] = ww[q];
+      x[tab_off_v(N1) + q] = xx[q];
+    }
+  }
+  return true;
+}
+
+// Per-device "uploaded" bookkeeping for one translation unit.
+struct UploadOnce {
+  std::mutex mu;
+  unsigned long long done = 0;  // bit per device ordinal (< 64)
+};
+
+}  // namespace ax

@@ -1,0 +1,51 @@
+"""Launch one AxLocal case a few times (for ncu captures and quick timing).
+
+  python -m paper_2504_07042_gb300.profile --N 7 --kind trilinear --prec f64dw \
+      --box 32 32 32 --launches 3
+
+Builds the perturbed-box mesh (or the parallelepiped box with --mesh
+parallelepiped), sets up the context, runs `--launches` AxLocal calls on the
+current stream and prints the CUDA-event time of each.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main():
+    import torch
+
+    from paper_2504_07042_gb300 import ax, inputs
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=7)
+    ap.add_argument("--kind", default="trilinear", choices=sorted(ax.KINDS))
+    ap.add_argument("--prec", default="f64dw", choices=sorted(ax.PRECS))
+    ap.add_argument("--mesh", default="trilinear", choices=["trilinear", "parallelepiped"])
+    ap.add_argument("--box", type=int, nargs=3, default=[32, 32, 32])
+    ap.add_argument("--launches", type=int, default=3)
+    a = ap.parse_args()
+    ex, ey, ez = a.box
+    V = inputs.parallelepiped_vertices(ex, ey, ez) if a.mesh == "parallelepiped" else \
+        inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), a.N, a.kind, a.prec)
+    X = torch.from_numpy(inputs.element_vectors(V.shape[0], a.N, seed=1)).to(dev, op.dtype)
+    Y = torch.empty_like(X)
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(a.launches):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        op.ax_local(X, Y, s)
+        t1.record(s)
+        torch.cuda.synchronize()
+        times.append(t0.elapsed_time(t1))
+    info = op.ax_query()
+    print(json.dumps({"E": op.E, "N": a.N, "kind": a.kind, "prec": a.prec, "ms": times,
+                      "gdofs": [op.E * op.n3 / (t * 1e-3) / 1e9 for t in times], "info": info}))
+
+
+if __name__ == "__main__":
+    main()

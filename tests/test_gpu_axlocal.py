@@ -1,0 +1,197 @@
+"""GPU parity of AxLocal (every geometry kind and precision) against the FP64
+CPU oracle, through the C ABI.
+
+Bar: relative max-norm ||Y_gpu - Y_oracle||_inf / ||Y_oracle||_inf <= 1e-12 for
+the float64 precisions (native FP64 and double-word), the tolerance the
+FP64 requirement states; FP32 kernels are held to 2e-5 (FP32 rounding of
+about 2N1+10 accumulated terms, eps_32 = 6e-8, with margin).
+"""
+import numpy as np
+import pytest
+
+from paper_2504_07042_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "f64dw": 1e-12, "fp32": 2e-5}
+KINDS = ["stored", "trilinear", "parallelepiped", "partial"]
+
+
+@pytest.fixture(scope="module")
+def ax():
+    from paper_2504_07042_gb300 import build
+
+    build.build()
+    from paper_2504_07042_gb300 import ax as _ax
+
+    return _ax
+
+
+def _mesh(kind, ex, ey, ez):
+    if kind == "parallelepiped":
+        return inputs.parallelepiped_vertices(ex, ey, ez)
+    return inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+
+
+def _run(ax, V, X, N, kind, prec):
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, prec)
+    dt = op.dtype
+    Xd = torch.from_numpy(X).to(dev, dt)
+    Yd = torch.full_like(Xd, float("nan"))
+    op.ax_local(Xd, Yd)
+    torch.cuda.synchronize()
+    out = Yd.double().cpu().numpy()
+    op.ax_destroy()
+    return out
+
+
+def _relerr(Y, Yref):
+    return np.max(np.abs(Y - Yref)) / np.max(np.abs(Yref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f64dw", "fp32"])
+@pytest.mark.parametrize("kind", KINDS)
+def test_c1_unit_cube_n7(ax, orc, kind, prec):
+    # 8x8x8 elements of the unit cube, interior vertices perturbed by U(-0.1h, 0.1h), N = 7
+    V = _mesh(kind, 8, 8, 8)
+    X = inputs.element_vectors(V.shape[0], 7, seed=1)
+    Yref, bad = orc.axlocal_vertices(V, X, 7)
+    assert bad == 0
+    Y = _run(ax, V, X, 7, kind, prec)
+    assert _relerr(Y, Yref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("prec", ["fp64", "f64dw", "fp32"])
+@pytest.mark.parametrize("kind", KINDS)
+def test_every_order_ragged_mesh(ax, orc, kind, prec, N):
+    # 3x2x2 = 12 elements: not a multiple of any elements-per-CTA count (ragged tail)
+    V = _mesh(kind, 3, 2, 2)
+    X = inputs.element_vectors(V.shape[0], N, seed=7 + N)
+    Yref, _ = orc.axlocal_vertices(V, X, N)
+    Y = _run(ax, V, X, N, kind, prec)
+    assert _relerr(Y, Yref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f64dw"])
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("N", [1, 3, 7, 15])
+def test_factors_match_eq7(ax, orc, kind, prec, N):
+    # the geometry step alone: Algorithm 2 / 3 / stored table vs Eq. 7 with the Eq. 9 Jacobian
+    V = _mesh(kind, 3, 2, 1)
+    Gref, _ = orc.factors(V, N)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, prec)
+    G = torch.empty((V.shape[0], 7, (N + 1) ** 3), dtype=torch.float64, device=dev)
+    op.ax_factors(G)
+    G = G.cpu().numpy()
+    scale = np.abs(Gref[:, :6]).max()
+    assert np.max(np.abs(G[:, :6] - Gref[:, :6])) <= 1e-13 * scale
+    assert np.max(np.abs(G[:, 6] - Gref[:, 6])) <= 1e-13 * np.abs(Gref[:, 6]).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f64dw"])
+def test_gpu_output_invariants(ax, prec):
+    # A 1 = 0 and y^T A x = x^T A y on the GPU results themselves
+    N = 5
+    V = _mesh("trilinear", 3, 3, 2)
+    E = V.shape[0]
+    ones = np.ones((E, (N + 1) ** 3))
+    X = inputs.element_vectors(E, N, seed=3)
+    Z = inputs.element_vectors(E, N, seed=4)
+    A1 = _run(ax, V, ones, N, "trilinear", prec)
+    AX = _run(ax, V, X, N, "trilinear", prec)
+    AZ = _run(ax, V, Z, N, "trilinear", prec)
+    assert np.abs(A1).max() < 1e-12 * np.abs(AX).max()
+    lhs, rhs = np.einsum("ij,ij->i", Z, AX), np.einsum("ij,ij->i", X, AZ)
+    assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.abs(lhs).max()
+
+
+def test_host_entry_point_matches_device(ax):
+    N = 7
+    V = _mesh("trilinear", 4, 3, 2)
+    X = inputs.element_vectors(V.shape[0], N, seed=1)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, "trilinear", "f64dw")
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.empty_like(Xd)
+    op.ax_local(Xd, Yd)
+    Yh = np.empty_like(X)
+    op.ax_local_host(X, Yh)
+    np.testing.assert_array_equal(Yh, Yd.cpu().numpy())
+
+
+def test_node_coords(ax, orc):
+    N = 4
+    V = _mesh("trilinear", 3, 2, 2)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, "stored", "fp64")
+    XYZ = torch.empty((V.shape[0], 3, (N + 1) ** 3), dtype=torch.float64, device=dev)
+    op.ax_node_coords(XYZ)
+    np.testing.assert_allclose(XYZ.cpu().numpy(), orc.nodal_coords(V, N), rtol=0, atol=1e-15)
+
+
+def test_empty_mesh_is_a_noop(ax):
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.zeros((0, 8, 3), dtype=torch.float64, device=dev), 7, "trilinear", "fp64")
+    X = torch.zeros((0, 512), dtype=torch.float64, device=dev)
+    op.ax_local(X, X.clone())
+
+
+def test_single_element(ax, orc):
+    V = _mesh("trilinear", 1, 1, 1)
+    X = inputs.element_vectors(1, 7, seed=5)
+    Yref, _ = orc.axlocal_vertices(V, X, 7)
+    for prec in ("fp64", "f64dw"):
+        assert _relerr(_run(ax, V, X, 7, "trilinear", prec), Yref) <= 1e-12
+
+
+def test_error_statuses(ax):
+    dev = torch.device("cuda:0")
+    V = inputs.box_vertices(2, 1, 1, perturb=0.0)
+    Vinv = V[:, [1, 0, 3, 2, 5, 4, 7, 6], :].copy()
+    with pytest.raises(ax.AxError) as ei:
+        ax.Ax(torch.from_numpy(Vinv).to(dev), 3, "trilinear", "fp64")
+    assert ei.value.status == ax.AX_EINVERTED
+    Vtri = inputs.box_vertices(3, 3, 3, perturb=0.1, seed=0)
+    with pytest.raises(ax.AxError) as ei:
+        ax.Ax(torch.from_numpy(Vtri).to(dev), 3, "parallelepiped", "fp64")
+    assert ei.value.status == ax.AX_ENOTPARALLELEPIPED
+    Vd = torch.from_numpy(V).to(dev)
+    for bad_n in (0, 16):
+        with pytest.raises(ax.AxError) as ei:
+            ax.Ax(Vd, bad_n, "trilinear", "fp64")
+        assert ei.value.status == ax.AX_EINVAL
+    with pytest.raises(ax.AxError) as ei:
+        ax.Ax(Vd, 3, 7, "fp64")
+    assert ei.value.status == ax.AX_EINVAL
+    op = ax.Ax(Vd, 3, "trilinear", "fp64")
+    X = torch.zeros((2, 64), dtype=torch.float64, device=dev)
+    with pytest.raises(ax.AxError) as ei:
+        op.ax_local(X, X)  # aliasing
+    assert ei.value.status == ax.AX_EINVAL
+    with pytest.raises(ax.AxError) as ei:
+        op.ax_local(None, X)
+    assert ei.value.status == ax.AX_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f64dw"])
+@pytest.mark.parametrize("kind", ["stored", "trilinear"])
+def test_full_size_sampled(ax, orc, kind, prec):
+    # the order-7 sweep workload (64x64x32 = 131072 elements, 67.1M local nodes),
+    # in the launch configuration the benchmark times; 256 sampled elements
+    # checked against the oracle element by element.
+    N = 7
+    ex, ey, ez = inputs.sweep_box(N)
+    V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    E = V.shape[0]
+    X = inputs.element_vectors(E, N, seed=1)
+    Y = _run(ax, V, X, N, kind, prec)
+    rng = np.random.default_rng(99)
+    idx = np.concatenate([[0, E - 1], rng.choice(E, 254, replace=False)])
+    Yref, _ = orc.axlocal_vertices(V[idx], X[idx], N)
+    assert _relerr(Y[idx], Yref) <= 1e-12
+    assert np.isfinite(Y).all()
