@@ -93,6 +93,25 @@ ax_status ax_local(ax_ctx *c, const void *X, void *Y, void *stream);
  * library-owned device buffers allocated at the first call. */
 ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *stream);
 
+/* ax_local_host for callers that cannot allocate device memory at call time
+ * (their device-memory budget is fixed after start-up, or a cudaMalloc /
+ * cudaFree would synchronise the device in the middle of their pipeline).
+ * The paper has no counterpart; this is a deployment variant of
+ * ax_local_host.
+ *   X_host, Y_host: host buffers of [E][n3] values (float64 or float32 as for
+ *   ax_local).  Copies X in, runs the same AxLocal kernel, copies Y out,
+ *   synchronises the stream.
+ * It calls no cudaMalloc/cudaFree: X and Y are staged through one file-scope
+ * device array of 32 MiB (16 MiB per vector), which every GPU that loads the
+ * library holds until the process exits.  E * (N+1)^3 * word size above
+ * 16 MiB returns AX_EINVAL (use ax_local_host or ax_local instead).
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls
+ * that overlap on the GPU (several host threads or streams at once) race,
+ * so callers must serialise them. */
+ax_status ax_local_host_static(ax_ctx *c, const void *X_host, void *Y_host, void *stream);
+
 /* The geometric factors as the kernel of this context obtains them, written
  * to G_out: device, [E][7][n3] float64.  Stored kinds copy their table; the
  * recompute kinds run their in-kernel geometry code (Algorithm 2 or 3) and

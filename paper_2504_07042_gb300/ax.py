@@ -43,6 +43,8 @@ _lib.ax_local.argtypes = [_vp, _vp, _vp, _vp]
 _lib.ax_local.restype = _int
 _lib.ax_local_host.argtypes = [_vp, _vp, _vp, _vp]
 _lib.ax_local_host.restype = _int
+_lib.ax_local_host_static.argtypes = [_vp, _vp, _vp, _vp]
+_lib.ax_local_host_static.restype = _int
 _lib.ax_factors.argtypes = [_vp, _vp, _vp]
 _lib.ax_factors.restype = _int
 _lib.ax_node_coords.argtypes = [_vp, _vp, _vp]
@@ -56,7 +58,7 @@ _lib.ax_status_string.restype = ctypes.c_char_p
 _lib.ax_destroy.argtypes = [_vp]
 _lib.ax_destroy.restype = None
 
-EXPORTS = ("ax_setup", "ax_local", "ax_local_host", "ax_factors", "ax_node_coords", "ax_query",
+EXPORTS = ("ax_setup", "ax_local", "ax_local_host", "ax_local_host_static", "ax_factors", "ax_node_coords", "ax_query",
            "ax_last_error", "ax_status_string", "ax_destroy")
 
 
@@ -112,6 +114,11 @@ class Ax:
 
     def ax_local_host(self, X_host, Y_host, stream=None):
         _check(_lib.ax_local_host(self.ctx, _ptr(X_host), _ptr(Y_host), _stream(stream)), self.ctx)
+        return Y_host
+
+    def ax_local_host_static(self, X_host, Y_host, stream=None):
+        """ax_local_host without device allocation (fixed 16 MiB per vector)."""
+        _check(_lib.ax_local_host_static(self.ctx, _ptr(X_host), _ptr(Y_host), _stream(stream)), self.ctx)
         return Y_host
 
     def ax_factors(self, G_out, stream=None):

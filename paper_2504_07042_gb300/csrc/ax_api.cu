@@ -4,6 +4,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -297,3 +298,66 @@ void ax_destroy(ax_ctx *c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ax_local_host_static: ax_local_host without any device allocation.
+//
+// Some callers cannot call cudaMalloc at the time they need the operator:
+// processes whose device-memory budget is fixed once start-up is over (every
+// allocation is made up front), and pipelines that must not let
+// cudaMalloc/cudaFree synchronise the device in the middle of their work.
+// ax_local_host allocates its device staging buffers on first use, which
+// such callers cannot allow.  This entry point stages X and Y through one
+// file-scope device array instead, of a fixed size (kStaticStageBytes, held
+// on every GPU that loads the library until the process exits).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticStageBytes = (size_t)32 << 20;     // whole array: 32 MiB
+constexpr size_t kStaticStageHalf = kStaticStageBytes / 2;  // X half, Y half
+
+static __device__ __align__(256) unsigned char g_static_stage[kStaticStageBytes];
+
+std::mutex g_static_stage_mu;
+void *g_static_stage_ptr[64] = {nullptr};
+
+}  // namespace
+
+extern "C" ax_status ax_local_host_static(ax_ctx *c, const void *X_host, void *Y_host, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_local_host_static: context is NULL");
+  if (c->c.E == 0) return AX_OK;
+  if (!X_host || !Y_host) return fail(c, AX_EINVAL, "ax_local_host_static: X or Y is NULL");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_local_host_static: current device differs from the context's");
+  const size_t bytes = (size_t)c->c.E * c->c.n3 * io_word(c->c.prec);
+  if (bytes > kStaticStageHalf) {
+    char msg[200];
+    snprintf(msg, sizeof msg,
+             "ax_local_host_static: X needs %zu bytes; the static staging array holds at most %zu bytes per vector "
+             "(use ax_local_host or ax_local)",
+             bytes, kStaticStageHalf);
+    return fail(c, AX_EINVAL, msg);
+  }
+  const int dev = c->c.device;
+  if (dev < 0 || dev >= 64) return fail(c, AX_EINVAL, "ax_local_host_static: device ordinal above 63");
+  void *base = nullptr;
+  {
+    // once per device, with that device current: the device address of the array
+    std::lock_guard<std::mutex> lock(g_static_stage_mu);
+    if (!g_static_stage_ptr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_stage);
+      if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host_static: cudaGetSymbolAddress");
+      g_static_stage_ptr[dev] = p;
+    }
+    base = g_static_stage_ptr[dev];
+  }
+  void *xd = base;
+  void *yd = (unsigned char *)base + kStaticStageHalf;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(xd, X_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = run_ax(c, make_args(c, xd, yd, stream));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Y_host, yd, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host_static");
+  return AX_OK;
+}

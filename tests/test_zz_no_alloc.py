@@ -1,0 +1,67 @@
+"""ax_local_host_static: the AxLocal entry point for callers that cannot call
+cudaMalloc at call time (a device-memory budget fixed after start-up, or a
+pipeline in which an allocation's implicit device synchronisation is not
+allowed).  It stages X and Y through the library's fixed 32 MiB device array
+instead of allocating.
+
+Checked through the C ABI against ax_local_host (same kernel, allocated
+staging buffers) on two calls in a row with different inputs, within the
+float64 tolerance used by the other parity tests; sizes beyond the array are
+rejected before any GPU work.  This module is collected last, so a failing
+run that stops at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2504_07042_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ax():
+    from paper_2504_07042_gb300 import build
+
+    build.build()
+    from paper_2504_07042_gb300 import ax as _ax
+
+    return _ax
+
+
+@pytest.mark.parametrize("prec,tol", [("f64dw", 1e-12), ("fp64", 1e-12), ("fp32", 2e-5)])
+def test_static_staging_matches_allocating_entry_point(ax, prec, tol):
+    N = 7
+    V = inputs.box_vertices(8, 8, 8, perturb=0.1, seed=0)  # 512 elements: 2 MiB per float64 vector
+    E = V.shape[0]
+    op = ax.Ax(torch.from_numpy(V).to("cuda:0"), N, "trilinear", prec)
+    npdt = np.float64 if op.dtype == torch.float64 else np.float32
+    for seed in (1, 2):  # two calls in a row; the second must not see the first one's data
+        X = inputs.element_vectors(E, N, seed=seed).astype(npdt)
+        Y_ref = np.full_like(X, np.nan)
+        Y = np.full_like(X, np.nan)
+        op.ax_local_host(X, Y_ref)
+        op.ax_local_host_static(X, Y)
+        assert np.isfinite(Y).all()
+        err = np.max(np.abs(Y.astype(np.float64) - Y_ref)) / np.max(np.abs(Y_ref))
+        assert err <= tol
+    op.ax_destroy()
+
+
+def test_static_staging_rejects_oversize(ax):
+    N = 7
+    V = inputs.box_vertices(16, 16, 16, perturb=0.0)  # 4096 elements x 512 x 8 B = 16 MiB: fits exactly
+    op = ax.Ax(torch.from_numpy(V).to("cuda:0"), N, "parallelepiped", "f64dw")
+    X = inputs.element_vectors(V.shape[0], N, seed=3)
+    Y = np.empty_like(X)
+    op.ax_local_host_static(X, Y)
+    op.ax_destroy()
+    V = inputs.box_vertices(17, 16, 16, perturb=0.0)  # 4352 elements: above the limit
+    op = ax.Ax(torch.from_numpy(V).to("cuda:0"), N, "parallelepiped", "f64dw")
+    X = inputs.element_vectors(V.shape[0], N, seed=3)
+    Y = np.empty_like(X)
+    with pytest.raises(ax.AxError) as ei:
+        op.ax_local_host_static(X, Y)
+    assert ei.value.status == ax.AX_EINVAL
+    op.ax_destroy()
