@@ -1,0 +1,177 @@
+// Throughput probes for the roofline denominators of the arithmetic pipes on
+// one GPU: FP64 DFMA, FP32 FFMA, FP64 DMMA m8n8k4, float64<->float32
+// conversion, mma.sync f16 and tf32, and a streaming copy.  Prints one JSON line.
+// All writes go to out[gtid] (sized grid*block); all loops bounded.
+#include <cstdio>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { printf("CUDA error %s at %d\n", cudaGetErrorString(e_), __LINE__); return 1; } } while (0)
+
+__global__ void k_dfma(double *out, int iters, double b, double c) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double a0 = g * 1e-9, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+  }
+  out[g] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+__global__ void k_ffma(double *out, int iters, float b, float c) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  float a0 = g * 1e-9f, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fmaf(a0, b, c); a1 = fmaf(a1, b, c); a2 = fmaf(a2, b, c); a3 = fmaf(a3, b, c);
+    a4 = fmaf(a4, b, c); a5 = fmaf(a5, b, c); a6 = fmaf(a6, b, c); a7 = fmaf(a7, b, c);
+  }
+  out[g] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+__global__ void k_dmma(double *out, int iters) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double a = 1.0 + (threadIdx.x & 7) * 1e-3, b = 0.5;
+  double c[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) c[q] = 0.0;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(c[2 * q]), "+d"(c[2 * q + 1]) : "d"(a), "d"(b));
+    }
+  }
+  double s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += c[q];
+  out[g] = s;
+}
+__global__ void k_cvt(double *out, int iters) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  long long b0 = __double_as_longlong(1.0 + g * 1e-9);
+  float acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+  for (int i = 0; i < iters; ++i) {
+    long long b = b0 + i;
+    acc0 += __double2float_rn(__longlong_as_double(b));
+    acc1 += __double2float_rn(__longlong_as_double(b + 7));
+    acc2 += __double2float_rn(__longlong_as_double(b + 13));
+    acc3 += __double2float_rn(__longlong_as_double(b + 29));
+  }
+  out[g] = acc0 + acc1 + acc2 + acc3;
+}
+__global__ void k_cvt_up(double *out, int iters) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  float f0 = 1.0f + g * 1e-7f;
+  double acc0 = 0, acc1 = 0;
+  unsigned u = __float_as_uint(f0);
+  for (int i = 0; i < iters; ++i) {
+    // 4 f32->f64 conversions; sums via integer ops on bit patterns to keep DADD out
+    long long t0 = __double_as_longlong((double)__uint_as_float(u + i));
+    long long t1 = __double_as_longlong((double)__uint_as_float(u + 3 * i));
+    long long t2 = __double_as_longlong((double)__uint_as_float(u + 5 * i));
+    long long t3 = __double_as_longlong((double)__uint_as_float(u + 7 * i));
+    acc0 = __longlong_as_double(__double_as_longlong(acc0) ^ t0 ^ t1);
+    acc1 = __longlong_as_double(__double_as_longlong(acc1) ^ t2 ^ t3);
+  }
+  out[g] = acc0 + acc1;
+}
+__global__ void k_hmma(double *out, int iters) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned a0 = 0x3c003c00u, a1 = a0, a2 = a0, a3 = a0, b0 = 0x3c003c00u, b1 = b0;
+  float c[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) c[q] = 0.f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                   : "+f"(c[4 * q]), "+f"(c[4 * q + 1]), "+f"(c[4 * q + 2]), "+f"(c[4 * q + 3])
+                   : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+  }
+  float s = 0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) s += c[q];
+  out[g] = s;
+}
+__global__ void k_tmma(double *out, int iters) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned a0 = 0x3f800000u, a1 = a0, a2 = a0, a3 = a0, b0 = a0, b1 = a0;
+  float c[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) c[q] = 0.f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                   : "+f"(c[4 * q]), "+f"(c[4 * q + 1]), "+f"(c[4 * q + 2]), "+f"(c[4 * q + 3])
+                   : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+  }
+  float s = 0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) s += c[q];
+  out[g] = s;
+}
+__global__ void k_copy(const double2 *__restrict__ a, double2 *__restrict__ b, size_t n) {
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = a[i];
+}
+__global__ void k_read(const double2 *__restrict__ a, double *out, size_t n) {
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  double s = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) { double2 v = a[i]; s += v.x + v.y; }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <class F>
+static float best_ms(F launch, int reps) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  launch();
+  cudaDeviceSynchronize();
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0);
+    launch();
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms; cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  return best;
+}
+
+int main() {
+  cudaDeviceProp p; CK(cudaGetDeviceProperties(&p, 0));
+  int sms = p.multiProcessorCount;
+  printf("{\"gpu\": \"%s\", \"sms\": %d, \"cc\": \"%d.%d\"", p.name, sms, p.major, p.minor);
+  const int blocks = sms * 8, threads = 256;
+  const long long nth = (long long)blocks * threads;
+  double *out; CK(cudaMalloc(&out, nth * sizeof(double)));
+  float ms;
+  int it;
+  it = 2048; ms = best_ms([&] { k_dfma<<<blocks, threads>>>(out, it, 0.999999, 1e-7); }, 3); CK(cudaGetLastError());
+  printf(", \"dfma_tflops\": %.4f", 2.0 * 8 * it * nth / (ms * 1e-3) / 1e12);
+  it = 65536; ms = best_ms([&] { k_ffma<<<blocks, threads>>>(out, it, 0.999999f, 1e-7f); }, 3); CK(cudaGetLastError());
+  printf(", \"ffma_tflops\": %.3f", 2.0 * 8 * it * nth / (ms * 1e-3) / 1e12);
+  it = 512; ms = best_ms([&] { k_dmma<<<blocks, threads>>>(out, it); }, 3); CK(cudaGetLastError());
+  printf(", \"dmma_m8n8k4_tflops\": %.4f", 512.0 * 4 * it * (nth / 32) / (ms * 1e-3) / 1e12);
+  it = 4096; ms = best_ms([&] { k_cvt<<<blocks, threads>>>(out, it); }, 3); CK(cudaGetLastError());
+  printf(", \"cvt_f64_to_f32_per_clk_sm_at_2070\": %.3f, \"cvt_f64_to_f32_G_per_s\": %.1f", 4.0 * it * nth / (ms * 1e-3) / (sms * 2.07e9), 4.0 * it * nth / (ms * 1e-3) / 1e9);
+  it = 4096; ms = best_ms([&] { k_cvt_up<<<blocks, threads>>>(out, it); }, 3); CK(cudaGetLastError());
+  printf(", \"cvt_f32_to_f64_G_per_s\": %.1f", 4.0 * it * nth / (ms * 1e-3) / 1e9);
+  it = 4096; ms = best_ms([&] { k_hmma<<<blocks, threads>>>(out, it); }, 3); CK(cudaGetLastError());
+  printf(", \"mma_sync_f16_m16n8k16_tflops\": %.1f", 2.0 * 16 * 8 * 16 * 4 * it * (nth / 32) / (ms * 1e-3) / 1e12);
+  it = 4096; ms = best_ms([&] { k_tmma<<<blocks, threads>>>(out, it); }, 3); CK(cudaGetLastError());
+  printf(", \"mma_sync_tf32_m16n8k8_tflops\": %.1f", 2.0 * 16 * 8 * 8 * 4 * it * (nth / 32) / (ms * 1e-3) / 1e12);
+  size_t n16 = (size_t)1 << 27;  // 2 GiB per buffer of double2
+  double2 *a, *b; CK(cudaMalloc(&a, n16 * 16)); CK(cudaMalloc(&b, n16 * 16));
+  CK(cudaMemset(a, 0, n16 * 16));
+  ms = best_ms([&] { k_copy<<<sms * 4, 512>>>(a, b, n16); }, 5); CK(cudaGetLastError());
+  printf(", \"copy_gbs\": %.1f", 2.0 * n16 * 16 / (ms * 1e-3) / 1e9);
+  ms = best_ms([&] { k_read<<<blocks, threads>>>(a, out, n16); }, 5); CK(cudaGetLastError());
+  printf(", \"read_gbs\": %.1f", 1.0 * n16 * 16 / (ms * 1e-3) / 1e9);
+  printf("}\n");
+  CK(cudaFree(a)); CK(cudaFree(b)); CK(cudaFree(out));
+  return 0;
+}
