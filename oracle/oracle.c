@@ -391,3 +391,125 @@ int orc_scatter(int64_t nlocal, const int64_t *gid, int64_t n_global, const doub
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Diagonal of every element matrix: diag[e][l] = e_l^T A^(e) e_l, by applying
+ * Algorithm 1 to each unit vector (the definition; O(n3^2) per element, for
+ * small meshes only).
+ * ---------------------------------------------------------------------- */
+int orc_diag(int64_t E, int N, const double *G, double *diag) {
+  const int N1 = N + 1, n3 = N1 * N1 * N1;
+  double xi[65], w[65], D[65 * 65];
+  if (orc_gll(N, xi, w, D)) return 1;
+  int fail = 0;
+#pragma omp parallel reduction(| : fail)
+  {
+    double *tmp = (double *)malloc(sizeof(double) * 5 * n3);
+    if (!tmp) fail = 1;
+    else {
+#pragma omp for schedule(static)
+      for (int64_t e = 0; e < E; ++e) {
+        double *x = tmp + 3 * n3, *y = tmp + 4 * n3;
+        for (int l = 0; l < n3; ++l) x[l] = 0.0;
+        for (int l = 0; l < n3; ++l) {
+          x[l] = 1.0;
+          axlocal_one(N1, D, G + (int64_t)7 * n3 * e, x, y, tmp, tmp + n3, tmp + 2 * n3);
+          diag[(int64_t)n3 * e + l] = y[l];
+          x[l] = 0.0;
+        }
+      }
+      free(tmp);
+    }
+  }
+  return fail;
+}
+
+/* ------------------------------------------------------------------------
+ * Preconditioned conjugate gradients (textbook PCG, e.g. Saad, "Iterative
+ * Methods for Sparse Linear Systems", Alg. 9.1) for the assembled Poisson
+ * system A = Q^T blkdiag(A^(e)) Q of Eq. 1, with homogeneous Dirichlet
+ * conditions imposed by masking: rows and columns of masked global nodes are
+ * removed (their entries of x, r, p are held at zero).
+ *   b, x: [n_global]; x is the initial guess on entry (masked entries ignored).
+ *   diag_global: NULL for plain CG, else the assembled diagonal (Jacobi).
+ *   Stops when ||r||_2 <= rtol ||b||_2 (b masked) or after maxit iterations.
+ * Returns 0 when converged, 1 when maxit was reached, -1 on error.
+ * ---------------------------------------------------------------------- */
+static void apply_assembled(int64_t E, int N, const double *G, const int64_t *gid, int64_t n_global,
+                            const unsigned char *mask, const double *p, double *w, double *Ul, double *Yl) {
+  const int64_t nl = E * (int64_t)(N + 1) * (N + 1) * (N + 1);
+  orc_scatter(nl, gid, n_global, p, Ul);
+  orc_axlocal(E, N, G, Ul, Yl);
+  orc_gather(nl, gid, n_global, Yl, w);
+  if (mask)
+    for (int64_t g = 0; g < n_global; ++g)
+      if (mask[g]) w[g] = 0.0;
+}
+
+static double dotv(int64_t n, const double *a, const double *b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+int orc_pcg(int64_t E, int N, const double *G, const int64_t *gid, int64_t n_global, const unsigned char *mask,
+            const double *b_in, double *x, const double *diag_global, double rtol, int maxit, int *iters,
+            double *relres) {
+  const int64_t nl = E * (int64_t)(N + 1) * (N + 1) * (N + 1);
+  double *b = (double *)malloc(sizeof(double) * n_global);
+  double *r = (double *)malloc(sizeof(double) * n_global);
+  double *z = (double *)malloc(sizeof(double) * n_global);
+  double *p = (double *)malloc(sizeof(double) * n_global);
+  double *w = (double *)malloc(sizeof(double) * n_global);
+  double *Ul = (double *)malloc(sizeof(double) * nl);
+  double *Yl = (double *)malloc(sizeof(double) * nl);
+  int status = -1;
+  if (!b || !r || !z || !p || !w || !Ul || !Yl) goto done;
+  for (int64_t g = 0; g < n_global; ++g) {
+    const int m = mask && mask[g];
+    b[g] = m ? 0.0 : b_in[g];
+    if (m) x[g] = 0.0;
+  }
+  {
+    const double bnorm = sqrt(dotv(n_global, b, b));
+    apply_assembled(E, N, G, gid, n_global, mask, x, w, Ul, Yl);
+    for (int64_t g = 0; g < n_global; ++g) r[g] = b[g] - w[g];
+    for (int64_t g = 0; g < n_global; ++g) z[g] = diag_global ? r[g] / diag_global[g] : r[g];
+    if (mask)
+      for (int64_t g = 0; g < n_global; ++g)
+        if (mask[g]) z[g] = 0.0;
+    for (int64_t g = 0; g < n_global; ++g) p[g] = z[g];
+    double rz = dotv(n_global, r, z);
+    double rnorm = sqrt(dotv(n_global, r, r));
+    int it = 0;
+    status = 1;
+    if (bnorm == 0.0 || rnorm <= rtol * bnorm) status = 0;
+    while (status == 1 && it < maxit) {
+      apply_assembled(E, N, G, gid, n_global, mask, p, w, Ul, Yl);
+      const double alpha = rz / dotv(n_global, p, w);
+      for (int64_t g = 0; g < n_global; ++g) {
+        x[g] += alpha * p[g];
+        r[g] -= alpha * w[g];
+      }
+      ++it;
+      rnorm = sqrt(dotv(n_global, r, r));
+      if (rnorm <= rtol * bnorm) {
+        status = 0;
+        break;
+      }
+      for (int64_t g = 0; g < n_global; ++g) z[g] = diag_global ? r[g] / diag_global[g] : r[g];
+      if (mask)
+        for (int64_t g = 0; g < n_global; ++g)
+          if (mask[g]) z[g] = 0.0;
+      const double rz_new = dotv(n_global, r, z);
+      const double beta = rz_new / rz;
+      rz = rz_new;
+      for (int64_t g = 0; g < n_global; ++g) p[g] = z[g] + beta * p[g];
+    }
+    *iters = it;
+    *relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  }
+done:
+  free(b); free(r); free(z); free(p); free(w); free(Ul); free(Yl);
+  return status;
+}

@@ -71,6 +71,12 @@ def lib():
         L.orc_gather.restype = c_int
         L.orc_scatter.argtypes = [i64, _ip, i64, _dp, _dp]
         L.orc_scatter.restype = c_int
+        L.orc_diag.argtypes = [i64, c_int, _dp, _dp]
+        L.orc_diag.restype = c_int
+        _u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+        L.orc_pcg.argtypes = [i64, c_int, _dp, _ip, i64, ctypes.c_void_p, _dp, _dp, ctypes.c_void_p, c_double,
+                              c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]
+        L.orc_pcg.restype = c_int
         _lib = L
     return _lib
 
@@ -207,3 +213,32 @@ def dense_element_matrix(Ge, N: int):
     g00, g01, g02, g11, g12, g22 = (np.diag(Ge[q]) for q in range(6))
     Gblk = np.block([[g00, g01, g02], [g01, g11, g12], [g02, g12, g22]])
     return Dfull.T @ Gblk @ Dfull
+
+
+def element_diagonals(G, N: int):
+    """diag[e][l] = e_l^T A^(e) e_l by Algorithm 1 on unit vectors (small meshes)."""
+    G = _f64(G)
+    E = G.shape[0]
+    d = np.zeros((E, (N + 1) ** 3))
+    if lib().orc_diag(E, int(N), G.reshape(-1), d.reshape(-1)):
+        raise MemoryError("oracle diag failed")
+    return d
+
+
+def pcg(G, gid, n_global: int, mask, b, N: int, x0=None, diag_global=None, rtol=1e-10, maxit=10000):
+    """Textbook (P)CG on the assembled, Dirichlet-masked system (Eq. 1).
+    Returns (x, iterations, relative residual, converged)."""
+    G = _f64(G)
+    E = G.shape[0]
+    gid = np.ascontiguousarray(gid, dtype=np.int64)
+    b = _f64(b)
+    x = np.zeros(int(n_global)) if x0 is None else _f64(x0).copy()
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    dg = None if diag_global is None else _f64(diag_global)
+    it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
+    st = lib().orc_pcg(E, int(N), G.reshape(-1), gid.reshape(-1), int(n_global),
+                       None if m is None else m.ctypes.data, b, x, None if dg is None else dg.ctypes.data,
+                       float(rtol), int(maxit), ctypes.byref(it), ctypes.byref(rr))
+    if st < 0:
+        raise MemoryError("oracle pcg failed")
+    return x, it.value, rr.value, st == 0

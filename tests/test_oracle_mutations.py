@@ -13,7 +13,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
-PINS = ["tests/test_oracle_gll.py", "tests/test_oracle_geometry.py", "tests/test_oracle_axlocal.py"]
+PINS = ["tests/test_oracle_gll.py", "tests/test_oracle_geometry.py", "tests/test_oracle_axlocal.py",
+        "tests/test_oracle_gs.py", "tests/test_oracle_pcg.py"]
 
 MUTATIONS = {
     "transposed_dhat_in_second_pass": ("y0 += D[n * N1 + i] * r", "y0 += D[i * N1 + n] * r"),
@@ -28,6 +29,10 @@ MUTATIONS = {
                            "w[i] = (double)(2.0L / ((long double)N * (N + 2) * LN[i] * LN[i]));"),
     "dhat_corner": ("else if (i == 0) d = -(long double)N * (N + 1) / 4.0L;", "else if (i == 0) d = -(long double)N * (N + 1) / 2.0L;"),
     "map_vertex_order": ("kron3(tv, sv, rv, row);", "kron3(rv, sv, tv, row);"),
+    "gather_overwrites": ("yg[gid[m]] += Yl[m];", "yg[gid[m]] = Yl[m];"),
+    "cg_beta_inverted": ("const double beta = rz_new / rz;", "const double beta = rz / rz_new;"),
+    "cg_mask_dropped": ("      if (mask[g]) w[g] = 0.0;", "      if (mask[g]) w[g] = w[g];"),
+    "diag_wrong_entry": ("diag[(int64_t)n3 * e + l] = y[l];", "diag[(int64_t)n3 * e + l] = y[(l + 1) % n3];"),
 }
 
 
