@@ -122,6 +122,47 @@ ax_status ax_factors(ax_ctx *c, double *G_out, void *stream);
  * XYZ_out: device, [E][3][n3] float64. */
 ax_status ax_node_coords(ax_ctx *c, double *XYZ_out, void *stream);
 
+/* Global numbering for gather-scatter: the binary global-to-local matrix Q
+ * of Eq. 1, Q[e*n3 + l][global_id[e][l]] = 1.
+ *   global_id: device, [E][n3] int64 in [0, n_global).
+ *   dirichlet_mask: device, [n_global] uint8 (1 = homogeneous Dirichlet node,
+ *   removed from the assembled system) or NULL.
+ * Builds, once, a CSR of the local copies of every global node in increasing
+ * local order (so every gather is a fixed-order, deterministic sum).
+ * Synchronises the stream.  AX_EINVAL if an id is out of range. */
+ax_status gs_setup(ax_ctx *c, const int64_t *global_id, int64_t n_global, const uint8_t *dirichlet_mask,
+                   void *stream);
+
+/* Y_local <- Q Q^T Y_local in place: each local copy of a global node is
+ * replaced by the sum of all its copies (Eq. 1 assembly, unmasked). */
+ax_status gs_assemble(ax_ctx *c, void *Y_local, void *stream);
+
+/* y_global = Q^T Y_local (sums of local copies; 0 on Dirichlet nodes). */
+ax_status gs_gather(ax_ctx *c, const void *Y_local, void *y_global, void *stream);
+
+/* U_local = Q u_global (copies the global value to every local copy). */
+ax_status gs_scatter(ax_ctx *c, const void *u_global, void *U_local, void *stream);
+
+/* GLL-lumped mass: Y_local = (w_i w_j w_k |J|) * F_local per node (the
+ * seventh factor of Eq. 7 times F); builds right-hand sides b = Q^T (w|J| f). */
+ax_status ax_mass(ax_ctx *c, const void *F_local, void *Y_local, void *stream);
+
+/* Element diagonals: diag_local[e][l] = e_l^T A^(e) e_l (for Jacobi). */
+ax_status ax_diag(ax_ctx *c, void *diag_local, void *stream);
+
+/* Conjugate gradients on the assembled system A = Q^T blkdiag(A^(e)) Q
+ * (Eq. 1) with the Dirichlet nodes of gs_setup removed, A applied with this
+ * context's AxLocal kernel.
+ *   b_global, x_global: device [n_global] (float64 for AX_FP64/AX_F64DW,
+ *   float32 otherwise); x_global is the initial guess and receives the
+ *   solution.  precond: 0 = none, 1 = Jacobi (assembled diagonal).
+ *   Stops when ||r||_2 <= rtol ||b||_2 or after maxit iterations
+ *   (AX_ENOTCONV).  *iters and *relres (host) report the outcome.
+ * Allocates its work vectors per call; reads one scalar per iteration to
+ * the host (the call synchronises). */
+ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol, int maxit, int precond, int *iters,
+                    double *relres, void *stream);
+
 /* Algorithmic cost of one ax_local call (per element): bytes moved to and
  * from HBM by the kernel's design, the paper's effective flops
  * F_ax = 12 N1^4 + 15 N1^3 (Table 2), and the arithmetic instructions the

@@ -49,6 +49,16 @@ _lib.ax_factors.argtypes = [_vp, _vp, _vp]
 _lib.ax_factors.restype = _int
 _lib.ax_node_coords.argtypes = [_vp, _vp, _vp]
 _lib.ax_node_coords.restype = _int
+_lib.gs_setup.argtypes = [_vp, _vp, _i64, _vp, _vp]
+_lib.gs_setup.restype = _int
+for _n in ("gs_gather", "gs_scatter", "ax_mass"):
+    getattr(_lib, _n).argtypes = [_vp, _vp, _vp, _vp]
+    getattr(_lib, _n).restype = _int
+for _n in ("gs_assemble", "ax_diag"):
+    getattr(_lib, _n).argtypes = [_vp, _vp, _vp]
+    getattr(_lib, _n).restype = _int
+_lib.pcg_solve.argtypes = [_vp, _vp, _vp, _dbl, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_dbl), _vp]
+_lib.pcg_solve.restype = _int
 _lib.ax_query.argtypes = [_vp, ctypes.POINTER(ax_info)]
 _lib.ax_query.restype = _int
 _lib.ax_last_error.argtypes = [_vp]
@@ -59,6 +69,7 @@ _lib.ax_destroy.argtypes = [_vp]
 _lib.ax_destroy.restype = None
 
 EXPORTS = ("ax_setup", "ax_local", "ax_local_host", "ax_local_host_static", "ax_factors", "ax_node_coords", "ax_query",
+           "gs_setup", "gs_assemble", "gs_gather", "gs_scatter", "ax_mass", "ax_diag", "pcg_solve",
            "ax_last_error", "ax_status_string", "ax_destroy")
 
 
@@ -128,6 +139,40 @@ class Ax:
     def ax_node_coords(self, XYZ_out, stream=None):
         _check(_lib.ax_node_coords(self.ctx, _ptr(XYZ_out), _stream(stream)), self.ctx)
         return XYZ_out
+
+    def gs_setup(self, global_id, n_global: int, dirichlet_mask=None, stream=None):
+        _check(_lib.gs_setup(self.ctx, _ptr(global_id), int(n_global), _ptr(dirichlet_mask), _stream(stream)),
+               self.ctx)
+        self.n_global = int(n_global)
+
+    def gs_assemble(self, Y_local, stream=None):
+        _check(_lib.gs_assemble(self.ctx, _ptr(Y_local), _stream(stream)), self.ctx)
+        return Y_local
+
+    def gs_gather(self, Y_local, y_global, stream=None):
+        _check(_lib.gs_gather(self.ctx, _ptr(Y_local), _ptr(y_global), _stream(stream)), self.ctx)
+        return y_global
+
+    def gs_scatter(self, u_global, U_local, stream=None):
+        _check(_lib.gs_scatter(self.ctx, _ptr(u_global), _ptr(U_local), _stream(stream)), self.ctx)
+        return U_local
+
+    def ax_mass(self, F_local, Y_local, stream=None):
+        _check(_lib.ax_mass(self.ctx, _ptr(F_local), _ptr(Y_local), _stream(stream)), self.ctx)
+        return Y_local
+
+    def ax_diag(self, diag_local, stream=None):
+        _check(_lib.ax_diag(self.ctx, _ptr(diag_local), _stream(stream)), self.ctx)
+        return diag_local
+
+    def pcg_solve(self, b_global, x_global, rtol=1e-8, maxit=10000, precond=1, stream=None, check=True):
+        """Returns (iterations, relative residual, status)."""
+        it, rr = _int(0), _dbl(0.0)
+        st = _lib.pcg_solve(self.ctx, _ptr(b_global), _ptr(x_global), float(rtol), int(maxit), int(precond),
+                            ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+        if check and st not in (AX_OK, AX_ENOTCONV):
+            _check(st, self.ctx)
+        return it.value, rr.value, st
 
     def ax_query(self) -> dict:
         info = ax_info()

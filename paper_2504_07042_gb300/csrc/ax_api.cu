@@ -49,6 +49,7 @@ void release(ax_ctx *c) {
   cudaFree(c->c.hx);
   cudaFree(c->c.hy);
   cudaFree(c->vtx);
+  ax::gs_free(c->c.gs);
   c->c.geo = c->c.lam = c->c.hx = c->c.hy = nullptr;
   c->vtx = nullptr;
 }
@@ -288,6 +289,123 @@ ax_status ax_query(const ax_ctx *c, ax_info *info) {
   info->pipe = (c->c.prec == AX_FP64) ? 0 : 1;
   if (c->c.prec == AX_F64DW) per_node = ax::dw_ops_per_node(c->c.N1, (int)c->c.kind);
   info->pipe_ops_per_element = per_node * n3;
+  return AX_OK;
+}
+
+ax_status gs_setup(ax_ctx *c, const int64_t *global_id, int64_t n_global, const uint8_t *dirichlet_mask,
+                   void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "gs_setup: context is NULL");
+  const int64_t n_local = c->c.E * (int64_t)c->c.n3;
+  if (n_global < 0 || (n_local > 0 && !global_id)) return fail(c, AX_EINVAL, "gs_setup: bad global ids");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "gs_setup: current device differs from the context's");
+  ax::gs_free(c->c.gs);
+  int64_t bad = 0;
+  cudaError_t e = ax::gs_build(c->c.gs, global_id, n_local, n_global, dirichlet_mask, (cudaStream_t)stream, &bad);
+  if (e != cudaSuccess) {
+    ax::gs_free(c->c.gs);
+    return cuda_fail(c, e, "gs_setup");
+  }
+  if (bad) {
+    ax::gs_free(c->c.gs);
+    char msg[120];
+    snprintf(msg, sizeof msg, "gs_setup: %lld global ids outside [0, n_global)", (long long)bad);
+    return fail(c, AX_EINVAL, msg);
+  }
+  return AX_OK;
+}
+
+static bool has_gs(ax_ctx *c) { return c->c.gs.off != nullptr; }
+
+ax_status gs_assemble(ax_ctx *c, void *Y_local, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "gs_assemble: context is NULL");
+  if (!has_gs(c)) return fail(c, AX_EINVAL, "gs_assemble: call gs_setup first");
+  if (c->c.gs.n_local && !Y_local) return fail(c, AX_EINVAL, "gs_assemble: Y is NULL");
+  cudaError_t e = ax::gs_assemble_run(c->c.gs, is_f64_io(c->c.prec), Y_local, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gs_assemble");
+  return AX_OK;
+}
+
+ax_status gs_gather(ax_ctx *c, const void *Y_local, void *y_global, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "gs_gather: context is NULL");
+  if (!has_gs(c)) return fail(c, AX_EINVAL, "gs_gather: call gs_setup first");
+  if (c->c.gs.n_global && (!Y_local || !y_global)) return fail(c, AX_EINVAL, "gs_gather: NULL vector");
+  cudaError_t e = ax::gs_gather_run(c->c.gs, is_f64_io(c->c.prec), Y_local, y_global, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gs_gather");
+  return AX_OK;
+}
+
+ax_status gs_scatter(ax_ctx *c, const void *u_global, void *U_local, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "gs_scatter: context is NULL");
+  if (!has_gs(c)) return fail(c, AX_EINVAL, "gs_scatter: call gs_setup first");
+  if (c->c.gs.n_local && (!u_global || !U_local)) return fail(c, AX_EINVAL, "gs_scatter: NULL vector");
+  cudaError_t e = ax::gs_scatter_run(c->c.gs, is_f64_io(c->c.prec), u_global, U_local, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gs_scatter");
+  return AX_OK;
+}
+
+ax_status ax_mass(ax_ctx *c, const void *F_local, void *Y_local, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_mass: context is NULL");
+  if (c->c.E == 0) return AX_OK;
+  if (!F_local || !Y_local) return fail(c, AX_EINVAL, "ax_mass: NULL vector");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_mass: current device differs from the context's");
+  cudaError_t e = ax::setup_mass(c->c, c->vtx, F_local, Y_local, is_f64_io(c->c.prec), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_mass");
+  return AX_OK;
+}
+
+ax_status ax_diag(ax_ctx *c, void *diag_local, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_diag: context is NULL");
+  if (c->c.E == 0) return AX_OK;
+  if (!diag_local) return fail(c, AX_EINVAL, "ax_diag: NULL vector");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_diag: current device differs from the context's");
+  cudaError_t e = ax::setup_diag(c->c, c->vtx, diag_local, is_f64_io(c->c.prec), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_diag");
+  return AX_OK;
+}
+
+ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol, int maxit, int precond, int *iters,
+                    double *relres, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "pcg_solve: context is NULL");
+  if (!has_gs(c)) return fail(c, AX_EINVAL, "pcg_solve: call gs_setup first");
+  if (!iters || !relres) return fail(c, AX_EINVAL, "pcg_solve: iters or relres is NULL");
+  if (precond != 0 && precond != 1) return fail(c, AX_EUNSUPPORTED, "pcg_solve: precond must be 0 (none) or 1 (Jacobi)");
+  if (!(rtol >= 0.0) || maxit < 0) return fail(c, AX_EINVAL, "pcg_solve: bad rtol or maxit");
+  if (c->c.gs.n_global && (!b_global || !x_global)) return fail(c, AX_EINVAL, "pcg_solve: NULL vector");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "pcg_solve: current device differs from the context's");
+  *iters = 0;
+  *relres = 0.0;
+  if (c->c.gs.n_global == 0) return AX_OK;
+  const bool f64 = is_f64_io(c->c.prec);
+  const size_t w = f64 ? 8 : 4;
+  cudaStream_t s = (cudaStream_t)stream;
+  void *diag_l = nullptr, *diag_g = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (precond == 1) {
+    e = cudaMalloc(&diag_l, w * c->c.gs.n_local + 8);
+    if (e == cudaSuccess) e = cudaMalloc(&diag_g, w * c->c.gs.n_global);
+    if (e == cudaSuccess) e = ax::setup_diag(c->c, c->vtx, diag_l, f64, s);
+    if (e == cudaSuccess) e = ax::gs_gather_run(c->c.gs, f64, diag_l, diag_g, s);
+  }
+  int conv = 0;
+  cudaError_t (*launch)(const ax::AxArgs &) = nullptr;
+  switch (c->c.prec) {
+    case AX_FP64: launch = ax::launch_ax_fp64; break;
+    case AX_FP32: launch = ax::launch_ax_fp32; break;
+    case AX_F64DW: launch = ax::launch_ax_dw; break;
+    default: break;
+  }
+  if (e == cudaSuccess && !launch) e = cudaErrorNotSupported;
+  if (e == cudaSuccess)
+    e = ax::pcg_run(c->c.gs, f64, make_args(c, nullptr, nullptr, stream), launch, b_global, x_global, diag_g, rtol,
+                    maxit, iters, relres, &conv, s);
+  cudaFree(diag_l);
+  cudaFree(diag_g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve");
+  if (!conv) {
+    char msg[120];
+    snprintf(msg, sizeof msg, "pcg_solve: not converged after %d iterations (relres %.3e)", *iters, *relres);
+    return fail(c, AX_ENOTCONV, msg);
+  }
   return AX_OK;
 }
 

@@ -1,0 +1,371 @@
+// Gather-scatter (Eq. 1: Q and Q^T) and the (P)CG driver around AxLocal.
+//
+// Q is stored as a CSR from global node to its local copies, built once on
+// the host in increasing local order, so every sum below has a fixed order
+// and the results are deterministic (no atomics).  Dirichlet nodes are
+// masked: their rows and columns are dropped from the assembled operator.
+//
+// CG is the textbook preconditioned conjugate gradient method (Jacobi
+// preconditioner = the assembled diagonal of the operator).  Scalars live
+// on the device; dot products are two-stage reductions with a fixed grid
+// (deterministic).  The host reads one scalar per iteration (||r||^2) for
+// the convergence test.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "ax_internal.h"
+
+namespace ax {
+namespace gs {
+
+constexpr int kRedBlocks = 1024;  // stage-1 blocks of every reduction (fixed: determinism)
+constexpr int kRedThreads = 256;
+
+template <typename T>
+__global__ void scatter_kernel(int64_t n_local, const int64_t *__restrict__ gid, const T *__restrict__ u,
+                               T *__restrict__ U) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n_local; m += (int64_t)gridDim.x * blockDim.x)
+    U[m] = u[gid[m]];
+}
+
+// y[g] = sum of the local copies of g (0 on masked nodes)
+template <typename T>
+__global__ void gather_kernel(int64_t n_global, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+                              const T *__restrict__ Y, T *__restrict__ y, const uint8_t *__restrict__ mask) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    y[g] = (mask && mask[g]) ? T(0) : s;
+  }
+}
+
+// Y <- Q Q^T Y in place
+template <typename T>
+__global__ void assemble_kernel(int64_t n_global, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+                                T *__restrict__ Y) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    for (int64_t q = off[g]; q < off[g + 1]; ++q) Y[idx[q]] = s;
+  }
+}
+
+// Fixed-order block reduction of v into out[blockIdx.x] (double accumulation).
+__device__ __forceinline__ void block_reduce_store(double v, double *out) {
+  __shared__ double sh[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < kRedThreads / 32 ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) *out = v;
+  }
+}
+
+// partial[b] = sum over this block's slice of a*b
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__restrict__ a, const T *__restrict__ b,
+                                                          double *__restrict__ partial) {
+  double s = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    s += (double)a[g] * (double)b[g];
+  block_reduce_store(s, partial + blockIdx.x);
+}
+
+// final stage: out = sum(partial[0..nb)) (one block)
+__global__ void __launch_bounds__(kRedThreads) finish_kernel(const double *__restrict__ partial, int nb,
+                                                             double *__restrict__ out) {
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) s += partial[q];
+  block_reduce_store(s, out);
+}
+
+// gather fused with the partial dot p . w
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    gather_dot_kernel(int64_t n_global, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+                      const T *__restrict__ Y, T *__restrict__ w, const uint8_t *__restrict__ mask,
+                      const T *__restrict__ p, double *__restrict__ partial) {
+  double d = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    if (mask && mask[g]) s = T(0);
+    w[g] = s;
+    d += (double)p[g] * (double)s;
+  }
+  block_reduce_store(d, partial + blockIdx.x);
+}
+
+// Scalars S: [0] rz, [1] pw, [2] rr, [3] bb, [4] rz_new
+// x += alpha p; r -= alpha w; z = r * inv_diag (0 on masked); partials of r.z and r.r
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    update_kernel(int64_t n, const double *__restrict__ S, const T *__restrict__ p, const T *__restrict__ w,
+                  T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, const T *__restrict__ inv_diag,
+                  const uint8_t *__restrict__ mask, double *__restrict__ part_rz, double *__restrict__ part_rr) {
+  const double alpha = S[0] / S[1];
+  double rz = 0.0, rr = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const T xg = x[g] + (T)alpha * p[g];
+    const T rg = r[g] - (T)alpha * w[g];
+    T zg = inv_diag ? rg * inv_diag[g] : rg;
+    if (mask && mask[g]) zg = T(0);
+    x[g] = xg;
+    r[g] = rg;
+    z[g] = zg;
+    rz += (double)rg * (double)zg;
+    rr += (double)rg * (double)rg;
+  }
+  block_reduce_store(rz, part_rz + blockIdx.x);
+  __syncthreads();
+  block_reduce_store(rr, part_rr + blockIdx.x);
+}
+
+// p = z + beta p, beta = rz_new / rz; the last block to finish moves rz_new into rz
+template <typename T>
+__global__ void direction_kernel(int64_t n, const double *__restrict__ S, const T *__restrict__ z,
+                                 T *__restrict__ p) {
+  const double beta = S[4] / S[0];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    p[g] = z[g] + (T)beta * p[g];
+}
+
+__global__ void shift_kernel(double *S) { S[0] = S[4]; }
+
+// initial: r = b - w (masked), z = r * inv_diag, p = z; partials of r.z, r.r, b.b
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    init_kernel(int64_t n, const T *__restrict__ b, const T *__restrict__ w, T *__restrict__ r, T *__restrict__ z,
+                T *__restrict__ p, const T *__restrict__ inv_diag, const uint8_t *__restrict__ mask,
+                double *__restrict__ part_rz, double *__restrict__ part_rr, double *__restrict__ part_bb) {
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const bool m = mask && mask[g];
+    const T bg = m ? T(0) : b[g];
+    const T rg = m ? T(0) : bg - w[g];
+    const T zg = m ? T(0) : (inv_diag ? rg * inv_diag[g] : rg);
+    r[g] = rg;
+    z[g] = zg;
+    p[g] = zg;
+    rz += (double)rg * (double)zg;
+    rr += (double)rg * (double)rg;
+    bb += (double)bg * (double)bg;
+  }
+  block_reduce_store(rz, part_rz + blockIdx.x);
+  __syncthreads();
+  block_reduce_store(rr, part_rr + blockIdx.x);
+  __syncthreads();
+  block_reduce_store(bb, part_bb + blockIdx.x);
+}
+
+template <typename T>
+__global__ void mask_zero_kernel(int64_t n, T *__restrict__ x, const uint8_t *__restrict__ mask) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    if (mask[g]) x[g] = T(0);
+}
+
+template <typename T>
+__global__ void invert_kernel(int64_t n, const T *__restrict__ d, T *__restrict__ inv, const uint8_t *__restrict__ mask) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    inv[g] = (mask && mask[g]) ? T(0) : T(1) / d[g];
+}
+
+inline unsigned grid_for(int64_t n, int block = 256) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 65535 * 16) g = 65535 * 16;
+  return (unsigned)g;
+}
+
+}  // namespace gs
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+cudaError_t gs_build(GsPlan &plan, const int64_t *gid_dev, int64_t n_local, int64_t n_global, const uint8_t *mask_dev,
+                     cudaStream_t s, int64_t *bad_ids) {
+  *bad_ids = 0;
+  std::vector<int64_t> gid((size_t)n_local);
+  cudaError_t e = cudaMemcpyAsync(gid.data(), gid_dev, sizeof(int64_t) * n_local, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  std::vector<int64_t> off((size_t)n_global + 1, 0);
+  for (int64_t m = 0; m < n_local; ++m) {
+    const int64_t g = gid[m];
+    if (g < 0 || g >= n_global) {
+      ++*bad_ids;
+      continue;
+    }
+    ++off[g + 1];
+  }
+  if (*bad_ids) return cudaSuccess;
+  for (int64_t g = 0; g < n_global; ++g) off[g + 1] += off[g];
+  std::vector<int64_t> idx((size_t)n_local), fill(off.begin(), off.end() - 1);
+  for (int64_t m = 0; m < n_local; ++m) idx[fill[gid[m]]++] = m;  // increasing local order per global node
+  plan.n_global = n_global;
+  plan.n_local = n_local;
+  e = cudaMalloc(&plan.off, sizeof(int64_t) * (n_global + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&plan.idx, sizeof(int64_t) * (n_local > 0 ? n_local : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&plan.gid, sizeof(int64_t) * (n_local > 0 ? n_local : 1));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(plan.off, off.data(), sizeof(int64_t) * (n_global + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_local)
+    e = cudaMemcpyAsync(plan.idx, idx.data(), sizeof(int64_t) * n_local, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_local)
+    e = cudaMemcpyAsync(plan.gid, gid_dev, sizeof(int64_t) * n_local, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && mask_dev) {
+    e = cudaMalloc(&plan.mask, n_global > 0 ? n_global : 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan.mask, mask_dev, n_global, cudaMemcpyDeviceToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors die with this scope
+  return e;
+}
+
+void gs_free(GsPlan &plan) {
+  cudaFree(plan.off);
+  cudaFree(plan.idx);
+  cudaFree(plan.gid);
+  cudaFree(plan.mask);
+  plan = GsPlan();
+}
+
+template <typename T>
+static cudaError_t gs_assemble_t(const GsPlan &p, void *Y, cudaStream_t s) {
+  if (p.n_global == 0) return cudaSuccess;
+  gs::assemble_kernel<T><<<gs::grid_for(p.n_global), 256, 0, s>>>(p.n_global, p.off, p.idx, (T *)Y);
+  return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t gs_gather_t(const GsPlan &p, const void *Y, void *y, cudaStream_t s) {
+  if (p.n_global == 0) return cudaSuccess;
+  gs::gather_kernel<T><<<gs::grid_for(p.n_global), 256, 0, s>>>(p.n_global, p.off, p.idx, (const T *)Y, (T *)y,
+                                                                 p.mask);
+  return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t gs_scatter_t(const GsPlan &p, const void *u, void *U, cudaStream_t s) {
+  if (p.n_local == 0) return cudaSuccess;
+  gs::scatter_kernel<T><<<gs::grid_for(p.n_local), 256, 0, s>>>(p.n_local, p.gid, (const T *)u, (T *)U);
+  return cudaGetLastError();
+}
+
+cudaError_t gs_assemble_run(const GsPlan &p, bool f64, void *Y, cudaStream_t s) {
+  return f64 ? gs_assemble_t<double>(p, Y, s) : gs_assemble_t<float>(p, Y, s);
+}
+cudaError_t gs_gather_run(const GsPlan &p, bool f64, const void *Y, void *y, cudaStream_t s) {
+  return f64 ? gs_gather_t<double>(p, Y, y, s) : gs_gather_t<float>(p, Y, y, s);
+}
+cudaError_t gs_scatter_run(const GsPlan &p, bool f64, const void *u, void *U, cudaStream_t s) {
+  return f64 ? gs_scatter_t<double>(p, u, U, s) : gs_scatter_t<float>(p, u, U, s);
+}
+
+// (P)CG on the assembled masked system.  apply(Ul, Yl) runs AxLocal.
+template <typename T>
+static cudaError_t pcg_t(const GsPlan &P, const AxArgs &base, cudaError_t (*launch)(const AxArgs &),
+                         const T *b, T *x, const T *diag_global, double rtol, int maxit, int *iters, double *relres,
+                         int *converged, cudaStream_t s) {
+  const int64_t n = P.n_global, nl = P.n_local;
+  const int RB = gs::kRedBlocks, RT = gs::kRedThreads;
+  T *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *Ul = nullptr, *Yl = nullptr, *inv = nullptr;
+  double *S = nullptr, *part = nullptr;
+  double *hS = nullptr;
+  cudaError_t e = cudaMalloc(&r, sizeof(T) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(T) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(T) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(T) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(T) * nl);
+  if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(T) * nl);
+  if (e == cudaSuccess && diag_global) e = cudaMalloc(&inv, sizeof(T) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 3 * RB);
+  if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * 8);
+  AxArgs a = base;
+  a.X = Ul;
+  a.Y = Yl;
+  a.stream = s;
+  *iters = 0;
+  *relres = 0.0;
+  *converged = 0;
+  if (e != cudaSuccess) goto done;
+  if (inv) {
+    gs::invert_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, diag_global, inv, P.mask);
+  }
+  if (P.mask) gs::mask_zero_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, x, P.mask);
+  // w = A x
+  gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, x, Ul);
+  e = launch(a);
+  if (e != cudaSuccess) goto done;
+  gs::gather_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, P.off, P.idx, Yl, w, P.mask);
+  gs::init_kernel<T><<<RB, RT, 0, s>>>(n, b, w, r, z, p, inv, P.mask, part, part + RB, part + 2 * RB);
+  gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 0);
+  gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
+  gs::finish_kernel<<<1, RT, 0, s>>>(part + 2 * RB, RB, S + 3);
+  e = cudaMemcpyAsync(hS, S, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) goto done;
+  {
+    const double bnorm = std::sqrt(hS[3]);
+    double rnorm = std::sqrt(hS[2]);
+    int it = 0;
+    if (bnorm == 0.0 || rnorm <= rtol * bnorm) {
+      *converged = 1;
+    } else {
+      while (it < maxit) {
+        gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, p, Ul);
+        e = launch(a);
+        if (e != cudaSuccess) goto done;
+        gs::gather_dot_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, Yl, w, P.mask, p, part);
+        gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 1);
+        gs::update_kernel<T><<<RB, RT, 0, s>>>(n, S, p, w, x, r, z, inv, P.mask, part, part + RB);
+        gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 4);
+        gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
+        e = cudaMemcpyAsync(hS + 2, S + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) goto done;
+        ++it;
+        rnorm = std::sqrt(hS[2]);
+        if (!(rnorm == rnorm)) break;  // NaN: give up, reported as not converged
+        if (rnorm <= rtol * bnorm) {
+          *converged = 1;
+          break;
+        }
+        gs::direction_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, S, z, p);
+        gs::shift_kernel<<<1, 1, 0, s>>>(S);
+      }
+    }
+    *iters = it;
+    *relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+done:
+  cudaFree(r);
+  cudaFree(z);
+  cudaFree(p);
+  cudaFree(w);
+  cudaFree(Ul);
+  cudaFree(Yl);
+  cudaFree(inv);
+  cudaFree(S);
+  cudaFree(part);
+  cudaFreeHost(hS);
+  return e;
+}
+
+cudaError_t pcg_run(const GsPlan &P, bool f64, const AxArgs &base, cudaError_t (*launch)(const AxArgs &),
+                    const void *b, void *x, const void *diag_global, double rtol, int maxit, int *iters,
+                    double *relres, int *converged, cudaStream_t s) {
+  if (f64)
+    return pcg_t<double>(P, base, launch, (const double *)b, (double *)x, (const double *)diag_global, rtol, maxit,
+                         iters, relres, converged, s);
+  return pcg_t<float>(P, base, launch, (const float *)b, (float *)x, (const float *)diag_global, rtol, maxit, iters,
+                      relres, converged, s);
+}
+
+}  // namespace ax

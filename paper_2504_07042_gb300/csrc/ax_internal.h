@@ -23,6 +23,15 @@ struct GllHost {
   double x[kMaxN1], w[kMaxN1], D[kMaxN1 * kMaxN1];
 };
 
+// Gather-scatter plan (Eq. 1's Q): CSR from global node to local copies.
+struct GsPlan {
+  int64_t n_global = 0, n_local = 0;
+  int64_t *off = nullptr;  // [n_global + 1]
+  int64_t *idx = nullptr;  // [n_local], local indices grouped by global node, increasing within a group
+  int64_t *gid = nullptr;  // [n_local], global id of every local node
+  uint8_t *mask = nullptr; // [n_global] Dirichlet mask or nullptr
+};
+
 struct Ctx {
   int64_t E = 0;
   int N = 0, N1 = 0, n3 = 0;
@@ -39,6 +48,7 @@ struct Ctx {
   // device staging buffers for ax_local_host
   void *hx = nullptr, *hy = nullptr;
   size_t hbytes = 0;
+  GsPlan gs;
   std::string err;
 };
 
@@ -79,5 +89,20 @@ double dw_ops_per_node(int N1, int kind);
 cudaError_t setup_geometry(const Ctx &c, const double *vertices, void *geo, void *lam, int *flags,
                            cudaStream_t s);
 cudaError_t setup_node_coords(const Ctx &c, const double *vertices, double *xyz, cudaStream_t s);
+// Y = w|J| F per node (GLL-lumped mass); F, Y float64 when f64 else float32.
+cudaError_t setup_mass(const Ctx &c, const double *vertices, const void *F, void *Y, bool f64, cudaStream_t s);
+// diag[e][l] = e_l^T A^(e) e_l from the factors (computed in FP64 into a temporary).
+cudaError_t setup_diag(const Ctx &c, const double *vertices, void *diag, bool f64, cudaStream_t s);
+
+// Gather-scatter and CG (ax_gs.cu).
+cudaError_t gs_build(GsPlan &plan, const int64_t *gid_dev, int64_t n_local, int64_t n_global, const uint8_t *mask_dev,
+                     cudaStream_t s, int64_t *bad_ids);
+void gs_free(GsPlan &plan);
+cudaError_t gs_assemble_run(const GsPlan &p, bool f64, void *Y, cudaStream_t s);
+cudaError_t gs_gather_run(const GsPlan &p, bool f64, const void *Y, void *y, cudaStream_t s);
+cudaError_t gs_scatter_run(const GsPlan &p, bool f64, const void *u, void *U, cudaStream_t s);
+cudaError_t pcg_run(const GsPlan &P, bool f64, const AxArgs &base, cudaError_t (*launch)(const AxArgs &),
+                    const void *b, void *x, const void *diag_global, double rtol, int maxit, int *iters,
+                    double *relres, int *converged, cudaStream_t s);
 
 }  // namespace ax

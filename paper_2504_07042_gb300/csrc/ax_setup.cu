@@ -194,6 +194,44 @@ __global__ void node_coords_kernel(int64_t E, int N1, const double *__restrict__
   for (int c = 0; c < 3; ++c) xyz[(e * 3 + c) * n3 + l] = X[c];
 }
 
+// Y = w_i w_j w_k det J * F at every node (the seventh factor times F).
+template <typename T>
+__global__ void mass_kernel(int64_t E, int N1, const double *__restrict__ V, const T *__restrict__ F, T *__restrict__ Y) {
+  const int64_t n3 = (int64_t)N1 * N1 * N1;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= E * n3) return;
+  const int64_t e = gidx / n3;
+  const int l = (int)(gidx % n3), i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+  const double *cx = c_x + tab_off_v(N1), *cw = c_w + tab_off_v(N1);
+  double J[9];
+  map_jacobian(V + 24 * e, cx[i], cx[j], cx[k], J);
+  Y[gidx] = (T)(cw[i] * cw[j] * cw[k] * det3(J) * (double)F[gidx]);
+}
+
+// Diagonal of the element matrix D^T G D at node l = (i,j,k):
+//   sum_n (D[n][i]^2 g00(n,j,k) + D[n][j]^2 g11(i,n,k) + D[n][k]^2 g22(i,j,n))
+//   + 2 (D[i][i] D[j][j] g01 + D[i][i] D[k][k] g02 + D[j][j] D[k][k] g12)(l)
+template <typename T>
+__global__ void diag_kernel(int64_t E, int N1, const double *__restrict__ G, T *__restrict__ out) {
+  const int64_t n3 = (int64_t)N1 * N1 * N1;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= E * n3) return;
+  const int64_t e = gidx / n3;
+  const int l = (int)(gidx % n3), i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+  const double *cD = c_D + tab_off_D(N1);
+  const double *Ge = G + e * 7 * n3;
+  double d = 0.0;
+  for (int n = 0; n < N1; ++n) {
+    const double a = cD[n * N1 + i], b = cD[n * N1 + j], c = cD[n * N1 + k];
+    d += a * a * Ge[0 * n3 + n + j * N1 + k * N1 * N1];
+    d += b * b * Ge[3 * n3 + i + n * N1 + k * N1 * N1];
+    d += c * c * Ge[5 * n3 + i + j * N1 + n * N1 * N1];
+  }
+  const double di = cD[i * N1 + i], dj = cD[j * N1 + j], dk = cD[k * N1 + k];
+  d += 2.0 * (di * dj * Ge[1 * n3 + l] + di * dk * Ge[2 * n3 + l] + dj * dk * Ge[4 * n3 + l]);
+  out[gidx] = (T)d;
+}
+
 static unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 }  // namespace setup
@@ -245,6 +283,42 @@ cudaError_t setup_node_coords(const Ctx &c, const double *V, double *xyz, cudaSt
   if (nodes == 0) return cudaSuccess;
   setup::node_coords_kernel<<<setup::grid_for(nodes, 256), 256, 0, s>>>(c.E, c.N1, V, xyz);
   return cudaGetLastError();
+}
+
+}  // namespace ax
+
+namespace ax {
+
+cudaError_t setup_mass(const Ctx &c, const double *V, const void *F, void *Y, bool f64, cudaStream_t s) {
+  const int64_t nodes = c.E * (int64_t)c.n3;
+  if (nodes == 0) return cudaSuccess;
+  if (f64)
+    setup::mass_kernel<double><<<setup::grid_for(nodes, 256), 256, 0, s>>>(c.E, c.N1, V, (const double *)F, (double *)Y);
+  else
+    setup::mass_kernel<float><<<setup::grid_for(nodes, 256), 256, 0, s>>>(c.E, c.N1, V, (const float *)F, (float *)Y);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_diag(const Ctx &c, const double *V, void *diag, bool f64, cudaStream_t s) {
+  const int64_t nodes = c.E * (int64_t)c.n3;
+  if (nodes == 0) return cudaSuccess;
+  double *G = nullptr;
+  int *flags = nullptr;
+  cudaError_t e = cudaMalloc(&G, sizeof(double) * 7 * nodes);
+  if (e == cudaSuccess) e = cudaMalloc(&flags, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);
+  if (e == cudaSuccess) {
+    setup::stored_factors_kernel<<<setup::grid_for(nodes, 256), 256, 0, s>>>(c.E, c.N1, V, G, setup::kF64, flags);
+    if (f64)
+      setup::diag_kernel<double><<<setup::grid_for(nodes, 256), 256, 0, s>>>(c.E, c.N1, G, (double *)diag);
+    else
+      setup::diag_kernel<float><<<setup::grid_for(nodes, 256), 256, 0, s>>>(c.E, c.N1, G, (float *)diag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(G);
+  cudaFree(flags);
+  return e;
 }
 
 }  // namespace ax
