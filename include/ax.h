@@ -163,6 +163,22 @@ ax_status ax_diag(ax_ctx *c, void *diag_local, void *stream);
 ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol, int maxit, int precond, int *iters,
                     double *relres, void *stream);
 
+/* Mixed-precision solve of the same system: FP64 iterative refinement
+ * around an inner Jacobi-PCG in float32 (the low-precision direction the
+ * paper names as future work, Sec. 7).
+ *   hi: context with AX_FP64 or AX_F64DW and gs_setup done; computes the
+ *       residual r = b - A x in FP64-accurate arithmetic each outer step.
+ *   lo: context of the same mesh (same E, N, vertices) with AX_FP32; runs
+ *       the inner solve A d = r / ||r||_inf to inner_rtol (at most max_inner
+ *       iterations); x += ||r||_inf d.
+ *   b_global, x_global: device float64 [n_global]; x is the initial guess.
+ *   Stops when ||r||_2 <= rtol ||b||_2 (AX_OK) or after max_outer outer
+ *   steps (AX_ENOTCONV).  *outer_iters, *inner_iters (total), *relres: host.
+ * Synchronises. */
+ax_status pcg_solve_mixed(ax_ctx *hi, ax_ctx *lo, const double *b_global, double *x_global, double rtol,
+                          double inner_rtol, int max_outer, int max_inner, int *outer_iters, int *inner_iters,
+                          double *relres, void *stream);
+
 /* Algorithmic cost of one ax_local call (per element): bytes moved to and
  * from HBM by the kernel's design, the paper's effective flops
  * F_ax = 12 N1^4 + 15 N1^3 (Table 2), and the arithmetic instructions the

@@ -59,6 +59,9 @@ for _n in ("gs_assemble", "ax_diag"):
     getattr(_lib, _n).restype = _int
 _lib.pcg_solve.argtypes = [_vp, _vp, _vp, _dbl, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_dbl), _vp]
 _lib.pcg_solve.restype = _int
+_lib.pcg_solve_mixed.argtypes = [_vp, _vp, _vp, _vp, _dbl, _dbl, _int, _int, ctypes.POINTER(_int),
+                                  ctypes.POINTER(_int), ctypes.POINTER(_dbl), _vp]
+_lib.pcg_solve_mixed.restype = _int
 _lib.ax_query.argtypes = [_vp, ctypes.POINTER(ax_info)]
 _lib.ax_query.restype = _int
 _lib.ax_last_error.argtypes = [_vp]
@@ -69,7 +72,7 @@ _lib.ax_destroy.argtypes = [_vp]
 _lib.ax_destroy.restype = None
 
 EXPORTS = ("ax_setup", "ax_local", "ax_local_host", "ax_local_host_static", "ax_factors", "ax_node_coords", "ax_query",
-           "gs_setup", "gs_assemble", "gs_gather", "gs_scatter", "ax_mass", "ax_diag", "pcg_solve",
+           "gs_setup", "gs_assemble", "gs_gather", "gs_scatter", "ax_mass", "ax_diag", "pcg_solve", "pcg_solve_mixed",
            "ax_last_error", "ax_status_string", "ax_destroy")
 
 
@@ -173,6 +176,18 @@ class Ax:
         if check and st not in (AX_OK, AX_ENOTCONV):
             _check(st, self.ctx)
         return it.value, rr.value, st
+
+    def pcg_solve_mixed(self, lo: "Ax", b_global, x_global, rtol=1e-8, inner_rtol=1e-3, max_outer=50,
+                        max_inner=5000, stream=None, check=True):
+        """FP64 refinement (this context) around a float32 inner PCG (lo).
+        Returns (outer iterations, total inner iterations, relative residual, status)."""
+        o, i, rr = _int(0), _int(0), _dbl(0.0)
+        st = _lib.pcg_solve_mixed(self.ctx, lo.ctx, _ptr(b_global), _ptr(x_global), float(rtol), float(inner_rtol),
+                                  int(max_outer), int(max_inner), ctypes.byref(o), ctypes.byref(i), ctypes.byref(rr),
+                                  _stream(stream))
+        if check and st not in (AX_OK, AX_ENOTCONV):
+            _check(st, self.ctx)
+        return o.value, i.value, rr.value, st
 
     def ax_query(self) -> dict:
         info = ax_info()

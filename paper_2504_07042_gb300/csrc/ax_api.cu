@@ -276,18 +276,9 @@ ax_status ax_query(const ax_ctx *c, ax_info *info) {
   }
   info->bytes_per_element = 2.0 * n3 * io + geo_bytes;
   info->flops_ax_per_element = 12.0 * N1 * N1 * N1 * N1 + 15.0 * n3;
-  // arithmetic instructions per node on the binding pipe (design counts):
-  // contractions 6*N1, geometric product 9, geometry by kind.
-  double geo_ops = 0.0;
-  switch (c->c.kind) {
-    case AX_GEOM_STORED: geo_ops = 0.0; break;
-    case AX_GEOM_PARALLELEPIPED: geo_ops = 7.0; break;
-    case AX_GEOM_TRILINEAR: geo_ops = 6 + 15 + 12 + 9 + 1 + 6 + 8; break;  // cols, K, adj, det, W, scale, division
-    case AX_GEOM_TRILINEAR_PARTIAL: geo_ops = 6 + 15 + 12 + 6; break;
-  }
-  double per_node = 6.0 * N1 + 9.0 + geo_ops;
+  // arithmetic instructions per node on the binding pipe (design counts)
+  const double per_node = ax::pipe_ops_per_node(c->c.N1, (int)c->c.kind, (int)c->c.prec);
   info->pipe = (c->c.prec == AX_FP64) ? 0 : 1;
-  if (c->c.prec == AX_F64DW) per_node = ax::dw_ops_per_node(c->c.N1, (int)c->c.kind);
   info->pipe_ops_per_element = per_node * n3;
   return AX_OK;
 }
@@ -405,6 +396,51 @@ ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol
     char msg[120];
     snprintf(msg, sizeof msg, "pcg_solve: not converged after %d iterations (relres %.3e)", *iters, *relres);
     return fail(c, AX_ENOTCONV, msg);
+  }
+  return AX_OK;
+}
+
+ax_status pcg_solve_mixed(ax_ctx *hi, ax_ctx *lo, const double *b_global, double *x_global, double rtol,
+                          double inner_rtol, int max_outer, int max_inner, int *outer_iters, int *inner_iters,
+                          double *relres, void *stream) {
+  if (!hi || !lo) return fail(nullptr, AX_EINVAL, "pcg_solve_mixed: context is NULL");
+  if (!is_f64_io(hi->c.prec)) return fail(hi, AX_EINVAL, "pcg_solve_mixed: hi must be AX_FP64 or AX_F64DW");
+  if (is_f64_io(lo->c.prec)) return fail(lo, AX_EINVAL, "pcg_solve_mixed: lo must be a float32 precision");
+  if (!has_gs(hi)) return fail(hi, AX_EINVAL, "pcg_solve_mixed: call gs_setup on hi first");
+  if (hi->c.E != lo->c.E || hi->c.N != lo->c.N) return fail(hi, AX_EINVAL, "pcg_solve_mixed: contexts differ in E or N");
+  if (!outer_iters || !inner_iters || !relres) return fail(hi, AX_EINVAL, "pcg_solve_mixed: NULL output pointer");
+  if (!(rtol >= 0.0) || !(inner_rtol > 0.0) || max_outer < 0 || max_inner < 1)
+    return fail(hi, AX_EINVAL, "pcg_solve_mixed: bad tolerances or iteration limits");
+  if (hi->c.gs.n_global && (!b_global || !x_global)) return fail(hi, AX_EINVAL, "pcg_solve_mixed: NULL vector");
+  if (!same_device(hi) || !same_device(lo)) return fail(hi, AX_EINVAL, "pcg_solve_mixed: device mismatch");
+  *outer_iters = *inner_iters = 0;
+  *relres = 0.0;
+  if (hi->c.gs.n_global == 0) return AX_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t (*lh)(const ax::AxArgs &) = hi->c.prec == AX_FP64 ? ax::launch_ax_fp64 : ax::launch_ax_dw;
+  cudaError_t (*ll)(const ax::AxArgs &) = nullptr;
+  switch (lo->c.prec) {
+    case AX_FP32: ll = ax::launch_ax_fp32; break;
+    default: return fail(lo, AX_EUNSUPPORTED, "pcg_solve_mixed: lo precision has no AxLocal kernel");
+  }
+  float *diag_l = nullptr, *diag_g = nullptr;
+  cudaError_t e = cudaMalloc(&diag_l, sizeof(float) * hi->c.gs.n_local + 8);
+  if (e == cudaSuccess) e = cudaMalloc(&diag_g, sizeof(float) * hi->c.gs.n_global);
+  if (e == cudaSuccess) e = ax::setup_diag(lo->c, lo->vtx, diag_l, false, s);
+  if (e == cudaSuccess) e = ax::gs_gather_run(hi->c.gs, false, diag_l, diag_g, s);
+  int conv = 0;
+  if (e == cudaSuccess)
+    e = ax::pcg_mixed_run(hi->c.gs, make_args(hi, nullptr, nullptr, stream), lh, make_args(lo, nullptr, nullptr, stream),
+                          ll, b_global, x_global, diag_g, rtol, inner_rtol, max_outer, max_inner, outer_iters,
+                          inner_iters, relres, &conv, s);
+  cudaFree(diag_l);
+  cudaFree(diag_g);
+  if (e != cudaSuccess) return cuda_fail(hi, e, "pcg_solve_mixed");
+  if (!conv) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "pcg_solve_mixed: not converged after %d outer / %d inner iterations (relres %.3e)",
+             *outer_iters, *inner_iters, *relres);
+    return fail(hi, AX_ENOTCONV, msg);
   }
   return AX_OK;
 }

@@ -1,0 +1,531 @@
+// AxLocal, fiber-per-thread design (templates over an arithmetic policy:
+// native FP64, native FP32, or double-word FP32 pairs).
+//
+// The whole element (EPB elements per CTA) sits in padded shared memory.
+// Every contraction of Algorithm 1 is done by a thread that owns a whole
+// fiber of the tensor in the contraction's direction, so the differentiation
+// matrix is read as a uniform constant-memory operand by all threads at once
+// (the constant-memory idea of Sec. 4.3.1, applied to all three directions),
+// and each fiber product uses the even-odd split of the centro-antisymmetric
+// D (D[N-i][N-j] = -D[i][j]): outputs i and N-i come from two half-length
+// dot products of the fiber's even and odd parts, nearly halving the
+// multiply-adds.
+//
+//   r-fibers  x0 = D_r x -> B0;   s-fibers  x1 = D_s x -> B1
+//   thread (i,j): t-fiber x2 = D_t x[i,j,:]; per node k the geometry
+//           (stored / Algorithm 2 / Algorithm 3 / partial) and
+//           (r,s,t) = G (x0,x1,x2); r -> B0, s -> B1; Y = D_t^T t
+//   r-fibers  Y += D_r^T r;   s-fibers  Y += D_s^T s;   Y to HBM.
+// Five barriers per element (two per k-layer in the layer-wise design).
+// Phase 3 (own t-fiber) needs no barrier after the geometry: each thread
+// reads and writes only its own fiber there.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ax_internal.h"
+#include "dw.cuh"
+#include "tables.cuh"
+
+namespace ax {
+namespace fiber {
+
+// ---------------------------------------------------------------------------
+// arithmetic policies
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Native {
+  using V = T;   // register value
+  using S = T;   // shared-memory / geometry-record word
+  using A = T;   // dot-product accumulator
+  using C = T;   // constant-table word
+  using IO = T;  // X, Y in HBM
+  static constexpr bool kRoll = false;  // short code: unroll the phase and k loops
+  __device__ static __forceinline__ V ld(const S *p) { return *p; }
+  __device__ static __forceinline__ S st(V v) { return v; }
+  __device__ static __forceinline__ V cst(const C *p) { return *p; }
+  __device__ static __forceinline__ V from_io(IO v) { return v; }
+  __device__ static __forceinline__ IO to_io(V v) { return v; }
+  __device__ static __forceinline__ V lit(double v) { return (T)v; }
+  __device__ static __forceinline__ A zero() { return T(0); }
+  __device__ static __forceinline__ void mac(A &a, V x, V y) { a = fma(x, y, a); }
+  __device__ static __forceinline__ V fin(A a) { return a; }
+  __device__ static __forceinline__ V add(V a, V b) { return a + b; }
+  __device__ static __forceinline__ V sub(V a, V b) { return a - b; }
+  __device__ static __forceinline__ V mul(V a, V b) { return a * b; }
+  __device__ static __forceinline__ V div(V a, V b) {
+    if constexpr (sizeof(T) == 4)
+      return __fdividef(a, b);  // 2-ulp quotient: the FP32 path's tolerance is 2e-5
+    else
+      return a / b;
+  }
+  __device__ static __forceinline__ V neg(V a) { return -a; }
+};
+
+struct DW {
+  using V = dw::dw;
+  using S = float2;
+  using A = dw::acc;
+  using C = float2;
+  using IO = double;
+  static constexpr bool kRoll = true;  // long code: keep the phase and k loops rolled (instruction cache)
+  __device__ static __forceinline__ V ld(const S *p) { return dw::from_float2(*p); }
+  __device__ static __forceinline__ S st(V v) { return make_float2(v.hi, v.lo); }
+  __device__ static __forceinline__ V cst(const C *p) { return dw::from_float2(*p); }
+  __device__ static __forceinline__ V from_io(IO v) { return dw::from_double(v); }
+  __device__ static __forceinline__ IO to_io(V v) { return dw::to_double(v); }
+  __device__ static __forceinline__ V lit(double v) { return dw::make((float)v, 0.0f); }  // exact small literals only
+  __device__ static __forceinline__ A zero() { return dw::acc_zero(); }
+  __device__ static __forceinline__ void mac(A &a, V x, V y) { dw::mac(a, x, y); }
+  __device__ static __forceinline__ V fin(A a) { return dw::fin(a); }
+  __device__ static __forceinline__ V add(V a, V b) { return dw::add(a, b); }
+  __device__ static __forceinline__ V sub(V a, V b) { return dw::sub(a, b); }
+  __device__ static __forceinline__ V mul(V a, V b) { return dw::mul(a, b); }
+  __device__ static __forceinline__ V div(V a, V b) { return dw::div(a, b); }
+  __device__ static __forceinline__ V neg(V a) { return dw::neg(a); }
+};
+
+template <class P>
+__device__ __forceinline__ typename P::V dot3(const typename P::V a[3], const typename P::V b[3]) {
+  typename P::A s = P::zero();
+  P::mac(s, a[0], b[0]);
+  P::mac(s, a[1], b[1]);
+  P::mac(s, a[2], b[2]);
+  return P::fin(s);
+}
+
+// a*b - c*d
+template <class P>
+__device__ __forceinline__ typename P::V det2(typename P::V a, typename P::V b, typename P::V c, typename P::V d) {
+  typename P::A s = P::zero();
+  P::mac(s, a, b);
+  P::mac(s, P::neg(c), d);
+  return P::fin(s);
+}
+
+// ---------------------------------------------------------------------------
+// even-odd fiber product: out = M in, M centro-antisymmetric (D or D^T).
+// Table block of order N1 (N1*N1 words), c = N1/2:
+//   rows i < c: [ A(i,0..c-1) | B(i,0..c-1) | M[i][c] if N1 odd ],
+//     A = (M[i][m] + M[i][N-m]) / 2,  B = (M[i][m] - M[i][N-m]) / 2
+//   row c (N1 odd): M[c][0..c-1]
+// out[i] = P + Q, out[N-i] = Q - P with P = sum A e + M[i][c] f[c], Q = sum B o,
+// e[m] = f[m] + f[N-m], o[m] = f[m] - f[N-m].
+// ---------------------------------------------------------------------------
+template <class P, int N1>
+__device__ __forceinline__ void contract(const typename P::C *__restrict__ eo, const typename P::V *in,
+                                         typename P::V *out) {
+  using V = typename P::V;
+  constexpr int c = N1 / 2;
+  constexpr bool odd = (N1 & 1) != 0;
+  V e[c], o[c];
+#pragma unroll
+  for (int m = 0; m < c; ++m) {
+    e[m] = P::add(in[m], in[N1 - 1 - m]);
+    o[m] = P::sub(in[m], in[N1 - 1 - m]);
+  }
+#pragma unroll
+  for (int i = 0; i < c; ++i) {
+    typename P::A p = P::zero(), q = P::zero();
+#pragma unroll
+    for (int m = 0; m < c; ++m) {
+      P::mac(p, P::cst(eo + i * N1 + m), e[m]);
+      P::mac(q, P::cst(eo + i * N1 + c + m), o[m]);
+    }
+    if constexpr (odd) P::mac(p, P::cst(eo + i * N1 + 2 * c), in[c]);
+    const V Pv = P::fin(p), Qv = P::fin(q);
+    out[i] = P::add(Pv, Qv);
+    out[N1 - 1 - i] = P::sub(Qv, Pv);
+  }
+  if constexpr (odd) {
+    typename P::A q = P::zero();
+#pragma unroll
+    for (int m = 0; m < c; ++m) P::mac(q, P::cst(eo + c * N1 + m), o[m]);
+    out[c] = P::fin(q);
+  }
+}
+
+template <int N1>
+struct Shape {
+  static constexpr int n3 = N1 * N1 * N1;
+  static constexpr int F = N1 * N1;  // fibers (threads) per element
+  static constexpr int EPB = (F >= 128) ? 1 : (128 / F);
+  static constexpr int threads = F * EPB;
+  static constexpr int P = N1 + 1;            // padded row
+  static constexpr int ES = N1 * N1 * P;      // padded element size (words)
+  __device__ static __forceinline__ int at(int i, int j, int k) { return i + P * (j + N1 * k); }
+};
+
+// ---------------------------------------------------------------------------
+// geometry (getFactors of Algorithm 4) in policy arithmetic
+//
+// Trilinear (Algorithm 2, true Jacobian): thread (i,j) holds the columns
+//   J0(t) = E0 + t E1  (E0, E1 depend on s = xi_j),
+//   J1(t) = F0 + t F1  (F0, F1 depend on r = xi_i),   J2 = Jc2(r, s),
+// so along its k-fiber (t = xi_k) every entry of K = J^T J is a polynomial
+// in t of degree <= 2 (K02, K12 affine, K22 constant) and so is
+// det J = J2 . (J0 x J1).  The prologue computes their coefficients once;
+// each node then costs 10 multiply-adds for K and det J, the adjugate
+// (Eq. 12) and one division:  (r,s,t) = adj(K) (lambda x), lambda = w/det J.
+// ---------------------------------------------------------------------------
+template <class P, int N1, int KIND>
+struct Geometry {
+  using V = typename P::V;
+  using S = typename P::S;
+  V wij;
+  V k00[3], k01[3], k11[3], k02[2], k12[2], k22, dt[3];  // polynomial coefficients in t
+  V h[7];
+  const S *gl = nullptr;
+
+  __device__ __forceinline__ void prologue(const S *sv, const typename P::C *xg, const typename P::C *wg, int i,
+                                           int j, const S *G_e, const S *lam_e) {
+    wij = P::mul(P::cst(wg + i), P::cst(wg + j));
+    if constexpr (KIND == AX_GEOM_STORED) {
+      gl = G_e;
+    } else if constexpr (KIND == AX_GEOM_PARALLELEPIPED) {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) h[q] = P::ld(sv + q);
+    } else {
+      V E0[3], E1[3], F0[3], F1[3], J2[3];
+      const V r = P::cst(xg + i), s = P::cst(xg + j);
+      const V one = P::lit(1.0), eighth = P::lit(0.125);
+      const V sm = P::sub(one, s), sp = P::add(one, s), rm = P::sub(one, r), rp = P::add(one, r);
+      const V u0 = P::mul(sm, eighth), u1 = P::mul(sp, eighth);
+      const V v0 = P::mul(rm, eighth), v1 = P::mul(rp, eighth);
+      const V w00 = P::mul(v0, sm), w10 = P::mul(v1, sm), w01 = P::mul(v0, sp), w11 = P::mul(v1, sp);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        auto Vx = [&](int v) { return P::ld(sv + 3 * v + c); };
+        // edges along r (a_bc), s (b_ac), t (c_ab) of the trilinear map (Eq. 8)
+        const V a00 = P::sub(Vx(1), Vx(0)), a10 = P::sub(Vx(3), Vx(2));
+        const V a01 = P::sub(Vx(5), Vx(4)), a11 = P::sub(Vx(7), Vx(6));
+        const V b00 = P::sub(Vx(2), Vx(0)), b10 = P::sub(Vx(3), Vx(1));
+        const V b01 = P::sub(Vx(6), Vx(4)), b11 = P::sub(Vx(7), Vx(5));
+        const V c00 = P::sub(Vx(4), Vx(0)), c10 = P::sub(Vx(5), Vx(1));
+        const V c01 = P::sub(Vx(6), Vx(2)), c11 = P::sub(Vx(7), Vx(3));
+        E0[c] = P::add(P::mul(u0, P::add(a00, a01)), P::mul(u1, P::add(a10, a11)));
+        E1[c] = P::add(P::mul(u0, P::sub(a01, a00)), P::mul(u1, P::sub(a11, a10)));
+        F0[c] = P::add(P::mul(v0, P::add(b00, b01)), P::mul(v1, P::add(b10, b11)));
+        F1[c] = P::add(P::mul(v0, P::sub(b01, b00)), P::mul(v1, P::sub(b11, b10)));
+        typename P::A q = P::zero();
+        P::mac(q, w00, c00);
+        P::mac(q, w10, c10);
+        P::mac(q, w01, c01);
+        P::mac(q, w11, c11);
+        J2[c] = P::fin(q);
+      }
+      // K = J^T J as polynomials in t
+      k00[0] = dot3<P>(E0, E0); k00[1] = P::add(dot3<P>(E0, E1), dot3<P>(E0, E1)); k00[2] = dot3<P>(E1, E1);
+      k11[0] = dot3<P>(F0, F0); k11[1] = P::add(dot3<P>(F0, F1), dot3<P>(F0, F1)); k11[2] = dot3<P>(F1, F1);
+      k01[0] = dot3<P>(E0, F0); k01[1] = P::add(dot3<P>(E0, F1), dot3<P>(E1, F0)); k01[2] = dot3<P>(E1, F1);
+      k02[0] = dot3<P>(E0, J2); k02[1] = dot3<P>(E1, J2);
+      k12[0] = dot3<P>(F0, J2); k12[1] = dot3<P>(F1, J2);
+      k22 = dot3<P>(J2, J2);
+      if constexpr (KIND == AX_GEOM_TRILINEAR) {
+        // det J(t) = J2 . (J0 x J1) = J0 . (J1 x J2): with w_a = F_a x J2
+        V w0[3], w1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+          w0[c] = det2<P>(F0[c1], J2[c2], F0[c2], J2[c1]);
+          w1[c] = det2<P>(F1[c1], J2[c2], F1[c2], J2[c1]);
+        }
+        dt[0] = dot3<P>(E0, w0);
+        dt[1] = P::add(dot3<P>(E0, w1), dot3<P>(E1, w0));
+        dt[2] = dot3<P>(E1, w1);
+      }
+      gl = lam_e;
+    }
+  }
+
+  __device__ __forceinline__ static V quad(const V c[3], V t) { return P::add(c[0], P::mul(t, P::add(c[1], P::mul(t, c[2])))); }
+  __device__ __forceinline__ static V lin(const V c[2], V t) { return P::add(c[0], P::mul(t, c[1])); }
+
+  // adjugate of K at t (symmetric: A00 A01 A02 A11 A12 A22)
+  __device__ __forceinline__ void adjK(V t, V A[6]) const {
+    const V K00 = quad(k00, t), K01 = quad(k01, t), K11 = quad(k11, t), K02 = lin(k02, t), K12 = lin(k12, t);
+    A[0] = det2<P>(K11, k22, K12, K12);
+    A[1] = det2<P>(K02, K12, K01, k22);
+    A[2] = det2<P>(K01, K12, K02, K11);
+    A[3] = det2<P>(K00, k22, K02, K02);
+    A[4] = det2<P>(K01, K02, K00, K12);
+    A[5] = det2<P>(K00, K11, K01, K01);
+  }
+
+  // (r, s, t) = G (x0, x1, x2) at local node l (t = xi_k, wk = w_k)
+  __device__ __forceinline__ void apply(int l, V t, V wk, const V xv[3], V out[3]) const {
+    constexpr int n3 = N1 * N1 * N1;
+    V A[6];
+    V y[3];
+    if constexpr (KIND == AX_GEOM_STORED) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) A[q] = P::ld(gl + q * n3 + l);
+      y[0] = xv[0]; y[1] = xv[1]; y[2] = xv[2];
+    } else if constexpr (KIND == AX_GEOM_PARALLELEPIPED) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) A[q] = h[q];
+      const V W = P::mul(wij, wk);
+      y[0] = P::mul(W, xv[0]); y[1] = P::mul(W, xv[1]); y[2] = P::mul(W, xv[2]);
+    } else {
+      adjK(t, A);
+      V lam;
+      if constexpr (KIND == AX_GEOM_TRILINEAR)
+        lam = P::div(P::mul(wij, wk), quad(dt, t));
+      else
+        lam = P::ld(gl + l);
+      y[0] = P::mul(lam, xv[0]); y[1] = P::mul(lam, xv[1]); y[2] = P::mul(lam, xv[2]);
+    }
+    const V gr[3] = {A[0], A[1], A[2]}, gs[3] = {A[1], A[3], A[4]}, gt[3] = {A[2], A[4], A[5]};
+    out[0] = dot3<P>(gr, y);
+    out[1] = dot3<P>(gs, y);
+    out[2] = dot3<P>(gt, y);
+  }
+
+  // g[0..5] = g00 g01 g02 g11 g12 g22 at local node l; returns the seventh factor w|J|.
+  __device__ __forceinline__ V factors(int l, V t, V wk, V g[6]) const {
+    constexpr int n3 = N1 * N1 * N1;
+    if constexpr (KIND == AX_GEOM_STORED) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) g[q] = P::ld(gl + q * n3 + l);
+      return P::ld(gl + 6 * n3 + l);
+    } else if constexpr (KIND == AX_GEOM_PARALLELEPIPED) {
+      const V W = P::mul(wij, wk);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) g[q] = P::mul(W, h[q]);
+      return P::mul(W, h[6]);
+    } else {
+      V A[6];
+      adjK(t, A);
+      const V W = P::mul(wij, wk);
+      V lam, wdet;
+      if constexpr (KIND == AX_GEOM_TRILINEAR) {
+        const V det = quad(dt, t);
+        lam = P::div(W, det);
+        wdet = P::mul(W, det);
+      } else {
+        lam = P::ld(gl + l);
+        wdet = P::div(P::mul(W, W), lam);
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) g[q] = P::mul(lam, A[q]);
+      return wdet;
+    }
+  }
+};
+
+template <int KIND>
+struct GeoWords {
+  static constexpr int value = (KIND == AX_GEOM_STORED) ? 0 : (KIND == AX_GEOM_PARALLELEPIPED ? kParWords : kVertexWords);
+};
+
+// ---------------------------------------------------------------------------
+// the kernel.  Tables (per translation unit, constant memory):
+//   c_eoD / c_eoDT: even-odd blocks of D and D^T, c_w, c_x: weights, points.
+// ---------------------------------------------------------------------------
+template <class P, int N1, int KIND>
+__global__ void __launch_bounds__(Shape<N1>::threads)
+    ax_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
+                    const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y) {
+  using Sh = Shape<N1>;
+  using V = typename P::V;
+  using S = typename P::S;
+  constexpr int n3 = Sh::n3, EPB = Sh::EPB, ES = Sh::ES;
+  constexpr int GW = GeoWords<KIND>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S *xs = (S *)smem_raw;       // [EPB][ES]: x, later Y
+  S *b0 = xs + EPB * ES;       // x0, later r
+  S *b1 = b0 + EPB * ES;       // x1, later s
+  __shared__ S sgeo[EPB][GW > 0 ? GW : 1];
+
+  const int tid = threadIdx.x;
+  const int z = tid / Sh::F, q = tid % Sh::F;
+  const int qa = q % N1, qb = q / N1;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+  const int64_t e = e0 + z;
+  const bool live = z < nel;
+  const typename P::C *eoD = c_eoD + tab_off_D(N1);
+  const typename P::C *eoDT = c_eoDT + tab_off_D(N1);
+  const typename P::C *cw = c_w + tab_off_v(N1);
+  const typename P::C *cx = c_x + tab_off_v(N1);
+
+  // pass 0: the CTA's elements (contiguous in HBM) into padded shared memory
+  for (int m = tid; m < nel * n3; m += Sh::threads) {
+    const int ze = m / n3, l = m % n3;
+    const int i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+    xs[ze * ES + Sh::at(i, j, k)] = P::st(P::from_io(X[e0 * n3 + m]));
+  }
+  if constexpr (GW > 0) {
+    for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
+  }
+  __syncthreads();
+
+  S *x_e = xs + z * ES, *r_e = b0 + z * ES, *s_e = b1 + z * ES;
+  // Six fiber products in two rolled phase loops (one code copy of the fiber
+  // product per matrix, D or D^T, so the constants stay immediate operands
+  // and the instruction footprint fits the instruction cache):
+  //   ph 0: r-fibers  D x -> B0 (x0)     ph 1: s-fibers  D x -> B1 (x1)
+  //   ph 2: t-fiber   D x -> X  (x2);  then per node the geometry and
+  //         (r,s,t) = G (x0,x1,x2): r -> B0, s -> B1, t -> X
+  //   ph 3: t-fiber   D^T t -> X (Y)   ph 4: r-fibers Y += D^T r
+  //   ph 5: s-fibers  Y += D^T s
+  const int fr = Sh::at(0, qa, qb), fs = Sh::at(qa, 0, qb), ft = Sh::at(qa, qb, 0);
+  constexpr int str_r = 1, str_s = Sh::P, str_t = Sh::P * N1;
+  auto forward = [&](int ph) {
+    if (ph == 2) __syncthreads();  // every r/s-fiber read of x is done before x is overwritten
+    S *dst = ph == 0 ? r_e : (ph == 1 ? s_e : x_e);
+    const int base = ph == 0 ? fr : (ph == 1 ? fs : ft);
+    const int stride = ph == 0 ? str_r : (ph == 1 ? str_s : str_t);
+    V fin_[N1], fout[N1];
+#pragma unroll
+    for (int n = 0; n < N1; ++n) fin_[n] = P::ld(x_e + base + n * stride);
+    contract<P, N1>(eoD, fin_, fout);
+#pragma unroll
+    for (int n = 0; n < N1; ++n) dst[base + n * stride] = P::st(fout[n]);
+  };
+  if constexpr (P::kRoll) {
+#pragma unroll 1
+    for (int ph = 0; ph < 3; ++ph) forward(ph);
+  } else {
+#pragma unroll
+    for (int ph = 0; ph < 3; ++ph) forward(ph);
+  }
+  __syncthreads();
+  {
+    // thread (i, j) = (qa, qb): geometry and G x along its own t-fiber
+    const int i = qa, j = qb;
+    Geometry<P, N1, KIND> gm;
+    gm.prologue(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+                (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
+    auto node = [&](int k) {
+      const int sidx = ft + k * str_t;
+      const V xv[3] = {P::ld(r_e + sidx), P::ld(s_e + sidx), P::ld(x_e + sidx)};
+      V o3[3];
+      if (live) {
+        gm.apply(i + j * N1 + k * N1 * N1, P::cst(cx + k), P::cst(cw + k), xv, o3);
+      } else {
+        o3[0] = o3[1] = o3[2] = P::lit(0.0);
+      }
+      r_e[sidx] = P::st(o3[0]);
+      s_e[sidx] = P::st(o3[1]);
+      x_e[sidx] = P::st(o3[2]);
+    };
+    if constexpr (P::kRoll) {
+#pragma unroll 1
+      for (int k = 0; k < N1; ++k) node(k);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N1; ++k) node(k);
+    }
+  }
+  auto transposed = [&](int ph) {
+    if (ph >= 4) __syncthreads();  // ph 4: all r, s written; ph 5: Y updates of ph 4 done
+    const S *src = ph == 3 ? x_e : (ph == 4 ? r_e : s_e);
+    const int base = ph == 3 ? ft : (ph == 4 ? fr : fs);
+    const int stride = ph == 3 ? str_t : (ph == 4 ? str_r : str_s);
+    V fin_[N1], fout[N1];
+#pragma unroll
+    for (int n = 0; n < N1; ++n) fin_[n] = P::ld(src + base + n * stride);
+    contract<P, N1>(eoDT, fin_, fout);
+    if (ph == 3) {
+#pragma unroll
+      for (int n = 0; n < N1; ++n) x_e[base + n * stride] = P::st(fout[n]);
+    } else {
+#pragma unroll
+      for (int n = 0; n < N1; ++n)
+        x_e[base + n * stride] = P::st(P::add(P::ld(x_e + base + n * stride), fout[n]));
+    }
+  };
+  if constexpr (P::kRoll) {
+#pragma unroll 1
+    for (int ph = 3; ph < 6; ++ph) transposed(ph);
+  } else {
+#pragma unroll
+    for (int ph = 3; ph < 6; ++ph) transposed(ph);
+  }
+  __syncthreads();
+
+  // pass 5: Y to HBM
+  for (int m = tid; m < nel * n3; m += Sh::threads) {
+    const int ze = m / n3, l = m % n3;
+    const int i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
+    Y[e0 * n3 + m] = P::to_io(P::ld(xs + ze * ES + Sh::at(i, j, k)));
+  }
+}
+
+// Factor export through the same geometry code: G_out [E][7][n3] float64.
+template <class P, int N1, int KIND>
+__global__ void __launch_bounds__(Shape<N1>::threads)
+    factors_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
+                         double *__restrict__ G) {
+  using Sh = Shape<N1>;
+  using V = typename P::V;
+  using S = typename P::S;
+  constexpr int n3 = Sh::n3, EPB = Sh::EPB;
+  constexpr int GW = GeoWords<KIND>::value;
+  __shared__ S sgeo[EPB][GW > 0 ? GW : 1];
+  const int tid = threadIdx.x;
+  const int z = tid / Sh::F, q = tid % Sh::F;
+  const int i = q % N1, j = q / N1;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+  const int64_t e = e0 + z;
+  const typename P::C *cw = c_w + tab_off_v(N1);
+  const typename P::C *cx = c_x + tab_off_v(N1);
+  if constexpr (GW > 0) {
+    for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
+  }
+  __syncthreads();
+  if (z >= nel) return;
+  Geometry<P, N1, KIND> gm;
+  gm.prologue(sgeo[z], cx, cw, i, j, KIND == AX_GEOM_STORED ? geo + e * 7 * n3 : nullptr,
+              KIND == AX_GEOM_TRILINEAR_PARTIAL ? lam + e * n3 : nullptr);
+  for (int k = 0; k < N1; ++k) {
+    const int l = i + j * N1 + k * N1 * N1;
+    V g[6];
+    const V gwj = gm.factors(l, P::cst(cx + k), P::cst(cw + k), g);
+    for (int w = 0; w < 6; ++w) G[(e * 7 + w) * n3 + l] = (double)P::to_io(g[w]);
+    G[(e * 7 + 6) * n3 + l] = (double)P::to_io(gwj);
+  }
+}
+
+template <class P, int N1, int KIND>
+cudaError_t launch_fiber_n(const AxArgs &a, double *G_out) {
+  using Sh = Shape<N1>;
+  const int64_t blocks = (a.E + Sh::EPB - 1) / Sh::EPB;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (G_out) {
+    factors_fiber_kernel<P, N1, KIND><<<(unsigned)blocks, Sh::threads, 0, a.stream>>>(
+        a.E, (const typename P::S *)a.geo, (const typename P::S *)a.lam, G_out);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)3 * Sh::EPB * Sh::ES * sizeof(typename P::S);
+  static bool attr_set = false;  // per instantiation; setting the attribute twice is harmless
+  if (!attr_set && smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(ax_fiber_kernel<P, N1, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  ax_fiber_kernel<P, N1, KIND><<<(unsigned)blocks, Sh::threads, smem, a.stream>>>(
+      a.E, (const typename P::S *)a.geo, (const typename P::S *)a.lam, (const typename P::IO *)a.X,
+      (typename P::IO *)a.Y);
+  return cudaGetLastError();
+}
+
+template <class P, int N1>
+cudaError_t launch_fiber_kinds(const AxArgs &a, double *G_out) {
+  switch (a.kind) {
+    case AX_GEOM_STORED: return launch_fiber_n<P, N1, AX_GEOM_STORED>(a, G_out);
+    case AX_GEOM_TRILINEAR: return launch_fiber_n<P, N1, AX_GEOM_TRILINEAR>(a, G_out);
+    case AX_GEOM_PARALLELEPIPED: return launch_fiber_n<P, N1, AX_GEOM_PARALLELEPIPED>(a, G_out);
+    case AX_GEOM_TRILINEAR_PARTIAL: return launch_fiber_n<P, N1, AX_GEOM_TRILINEAR_PARTIAL>(a, G_out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fiber
+}  // namespace ax

@@ -265,96 +265,109 @@ cudaError_t gs_scatter_run(const GsPlan &p, bool f64, const void *u, void *U, cu
   return f64 ? gs_scatter_t<double>(p, u, U, s) : gs_scatter_t<float>(p, u, U, s);
 }
 
-// (P)CG on the assembled masked system.  apply(Ul, Yl) runs AxLocal.
+// Work vectors of one CG solve (allocated once per solve, reused across the
+// inner solves of the mixed-precision driver).
 template <typename T>
-static cudaError_t pcg_t(const GsPlan &P, const AxArgs &base, cudaError_t (*launch)(const AxArgs &),
-                         const T *b, T *x, const T *diag_global, double rtol, int maxit, int *iters, double *relres,
-                         int *converged, cudaStream_t s) {
+struct PcgWork {
+  int64_t n = 0, nl = 0;
+  T *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *Ul = nullptr, *Yl = nullptr, *inv = nullptr;
+  double *S = nullptr, *part = nullptr, *hS = nullptr;
+  cudaError_t alloc(int64_t n_, int64_t nl_, bool jacobi) {
+    n = n_;
+    nl = nl_;
+    cudaError_t e = cudaMalloc(&r, sizeof(T) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(T) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(T) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(T) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(T) * nl);
+    if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(T) * nl);
+    if (e == cudaSuccess && jacobi) e = cudaMalloc(&inv, sizeof(T) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 3 * gs::kRedBlocks);
+    if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * 8);
+    return e;
+  }
+  void release() {
+    cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(w); cudaFree(Ul); cudaFree(Yl); cudaFree(inv);
+    cudaFree(S); cudaFree(part); cudaFreeHost(hS);
+    *this = PcgWork();
+  }
+};
+
+// (P)CG on the assembled masked system with work W (W.inv already holds the
+// inverted diagonal when Jacobi is on).  launch() runs AxLocal on W.Ul -> W.Yl.
+template <typename T>
+static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*launch)(const AxArgs &), PcgWork<T> &W,
+                            const T *b, T *x, double rtol, int maxit, int *iters, double *relres, int *converged,
+                            cudaStream_t s) {
   const int64_t n = P.n_global, nl = P.n_local;
   const int RB = gs::kRedBlocks, RT = gs::kRedThreads;
-  T *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *Ul = nullptr, *Yl = nullptr, *inv = nullptr;
-  double *S = nullptr, *part = nullptr;
-  double *hS = nullptr;
-  cudaError_t e = cudaMalloc(&r, sizeof(T) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(T) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(T) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(T) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(T) * nl);
-  if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(T) * nl);
-  if (e == cudaSuccess && diag_global) e = cudaMalloc(&inv, sizeof(T) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 3 * RB);
-  if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * 8);
   AxArgs a = base;
-  a.X = Ul;
-  a.Y = Yl;
+  a.X = W.Ul;
+  a.Y = W.Yl;
   a.stream = s;
   *iters = 0;
   *relres = 0.0;
   *converged = 0;
-  if (e != cudaSuccess) goto done;
-  if (inv) {
-    gs::invert_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, diag_global, inv, P.mask);
-  }
+  double *S = W.S, *part = W.part, *hS = W.hS;
   if (P.mask) gs::mask_zero_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, x, P.mask);
-  // w = A x
-  gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, x, Ul);
-  e = launch(a);
-  if (e != cudaSuccess) goto done;
-  gs::gather_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, P.off, P.idx, Yl, w, P.mask);
-  gs::init_kernel<T><<<RB, RT, 0, s>>>(n, b, w, r, z, p, inv, P.mask, part, part + RB, part + 2 * RB);
+  gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, x, W.Ul);
+  cudaError_t e = launch(a);
+  if (e != cudaSuccess) return e;
+  gs::gather_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask);
+  gs::init_kernel<T><<<RB, RT, 0, s>>>(n, b, W.w, W.r, W.z, W.p, W.inv, P.mask, part, part + RB, part + 2 * RB);
   gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 0);
   gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
   gs::finish_kernel<<<1, RT, 0, s>>>(part + 2 * RB, RB, S + 3);
   e = cudaMemcpyAsync(hS, S, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) goto done;
-  {
-    const double bnorm = std::sqrt(hS[3]);
-    double rnorm = std::sqrt(hS[2]);
-    int it = 0;
-    if (bnorm == 0.0 || rnorm <= rtol * bnorm) {
-      *converged = 1;
-    } else {
-      while (it < maxit) {
-        gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, p, Ul);
-        e = launch(a);
-        if (e != cudaSuccess) goto done;
-        gs::gather_dot_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, Yl, w, P.mask, p, part);
-        gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 1);
-        gs::update_kernel<T><<<RB, RT, 0, s>>>(n, S, p, w, x, r, z, inv, P.mask, part, part + RB);
-        gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 4);
-        gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
-        e = cudaMemcpyAsync(hS + 2, S + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) goto done;
-        ++it;
-        rnorm = std::sqrt(hS[2]);
-        if (!(rnorm == rnorm)) break;  // NaN: give up, reported as not converged
-        if (rnorm <= rtol * bnorm) {
-          *converged = 1;
-          break;
-        }
-        gs::direction_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, S, z, p);
-        gs::shift_kernel<<<1, 1, 0, s>>>(S);
+  if (e != cudaSuccess) return e;
+  const double bnorm = std::sqrt(hS[3]);
+  double rnorm = std::sqrt(hS[2]);
+  int it = 0;
+  if (bnorm == 0.0 || rnorm <= rtol * bnorm) {
+    *converged = 1;
+  } else {
+    while (it < maxit) {
+      gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, W.p, W.Ul);
+      e = launch(a);
+      if (e != cudaSuccess) return e;
+      gs::gather_dot_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask, W.p, part);
+      gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 1);
+      gs::update_kernel<T><<<RB, RT, 0, s>>>(n, S, W.p, W.w, x, W.r, W.z, W.inv, P.mask, part, part + RB);
+      gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 4);
+      gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
+      e = cudaMemcpyAsync(hS + 2, S + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return e;
+      ++it;
+      rnorm = std::sqrt(hS[2]);
+      if (!(rnorm == rnorm)) break;  // NaN: reported as not converged
+      if (rnorm <= rtol * bnorm) {
+        *converged = 1;
+        break;
       }
+      gs::direction_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, S, W.z, W.p);
+      gs::shift_kernel<<<1, 1, 0, s>>>(S);
     }
-    *iters = it;
-    *relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
   }
+  *iters = it;
+  *relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-done:
-  cudaFree(r);
-  cudaFree(z);
-  cudaFree(p);
-  cudaFree(w);
-  cudaFree(Ul);
-  cudaFree(Yl);
-  cudaFree(inv);
-  cudaFree(S);
-  cudaFree(part);
-  cudaFreeHost(hS);
+  return e;
+}
+
+template <typename T>
+static cudaError_t pcg_t(const GsPlan &P, const AxArgs &base, cudaError_t (*launch)(const AxArgs &), const T *b, T *x,
+                         const T *diag_global, double rtol, int maxit, int *iters, double *relres, int *converged,
+                         cudaStream_t s) {
+  PcgWork<T> W;
+  cudaError_t e = W.alloc(P.n_global, P.n_local, diag_global != nullptr);
+  if (e == cudaSuccess && diag_global)
+    gs::invert_kernel<T><<<gs::grid_for(P.n_global), 256, 0, s>>>(P.n_global, diag_global, W.inv, P.mask);
+  if (e == cudaSuccess) e = pcg_core<T>(P, base, launch, W, b, x, rtol, maxit, iters, relres, converged, s);
+  W.release();
   return e;
 }
 
@@ -366,6 +379,148 @@ cudaError_t pcg_run(const GsPlan &P, bool f64, const AxArgs &base, cudaError_t (
                          iters, relres, converged, s);
   return pcg_t<float>(P, base, launch, (const float *)b, (float *)x, (const float *)diag_global, rtol, maxit, iters,
                       relres, converged, s);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision: FP64 iterative refinement around an inner FP32 solve.
+//   r = b - A x            (hi context: FP64-accurate AxLocal, float64 vectors)
+//   A d = r / sigma        (lo context: inner Jacobi-PCG in float32 to inner_rtol)
+//   x = x + sigma d        (sigma = ||r||_inf keeps the float32 data near 1)
+// until ||r||_2 <= rtol ||b||_2.
+// ---------------------------------------------------------------------------
+namespace gs {
+__global__ void residual_kernel(int64_t n, const double *__restrict__ b, const double *__restrict__ w,
+                                double *__restrict__ r, const uint8_t *__restrict__ mask) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    r[g] = (mask && mask[g]) ? 0.0 : b[g] - w[g];
+}
+__global__ void __launch_bounds__(kRedThreads) norms_kernel(int64_t n, const double *__restrict__ r,
+                                                            double *__restrict__ part2, double *__restrict__ partinf) {
+  double s = 0.0, m = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    s += r[g] * r[g];
+    m = fmax(m, fabs(r[g]));
+  }
+  block_reduce_store(s, part2 + blockIdx.x);
+  __syncthreads();
+  // max: fixed-order warp/block max
+  __shared__ double sh[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = m;
+  __syncthreads();
+  if (wid == 0) {
+    m = lane < kRedThreads / 32 ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (lane == 0) partinf[blockIdx.x] = m;
+  }
+}
+__global__ void __launch_bounds__(kRedThreads) finish_max_kernel(const double *__restrict__ part, int nb,
+                                                                 double *__restrict__ out) {
+  __shared__ double sh[kRedThreads];
+  double m = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) m = fmax(m, part[q]);
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+__global__ void scale_down_kernel(int64_t n, const double *__restrict__ r, const double *__restrict__ sig,
+                                  float *__restrict__ r32, float *__restrict__ d32) {
+  const double inv = *sig > 0.0 ? 1.0 / *sig : 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    r32[g] = (float)(r[g] * inv);
+    d32[g] = 0.0f;
+  }
+}
+__global__ void correct_kernel(int64_t n, const float *__restrict__ d32, const double *__restrict__ sig,
+                               double *__restrict__ x) {
+  const double sg = *sig;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    x[g] += sg * (double)d32[g];
+}
+}  // namespace gs
+
+cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launch_hi)(const AxArgs &),
+                          const AxArgs &lo, cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x,
+                          const float *diag_lo, double rtol, double inner_rtol, int max_outer, int max_inner,
+                          int *outer, int *inner_total, double *relres, int *converged, cudaStream_t s) {
+  const int64_t n = P.n_global, nl = P.n_local;
+  const int RB = gs::kRedBlocks, RT = gs::kRedThreads;
+  PcgWork<float> W;
+  double *r = nullptr, *w = nullptr, *Ul = nullptr, *Yl = nullptr, *S = nullptr, *part = nullptr, *hS = nullptr;
+  float *r32 = nullptr, *d32 = nullptr;
+  *outer = 0;
+  *inner_total = 0;
+  *relres = 0.0;
+  *converged = 0;
+  cudaError_t e = W.alloc(n, nl, diag_lo != nullptr);
+  if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(double) * nl);
+  if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(double) * nl);
+  if (e == cudaSuccess) e = cudaMalloc(&r32, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&d32, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 2 * RB);
+  if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * 8);
+  if (e == cudaSuccess && diag_lo)
+    gs::invert_kernel<float><<<gs::grid_for(n), 256, 0, s>>>(n, diag_lo, W.inv, P.mask);
+  AxArgs ah = hi;
+  ah.X = Ul;
+  ah.Y = Yl;
+  ah.stream = s;
+  double bnorm = 0.0;
+  if (e == cudaSuccess) {
+    // ||b|| over the unmasked nodes: r = b - 0 (masked)
+    gs::mask_zero_kernel<double><<<gs::grid_for(n), 256, 0, s>>>(n, x, P.mask);
+    e = cudaMemsetAsync(w, 0, sizeof(double) * n, s);
+    gs::residual_kernel<<<gs::grid_for(n), 256, 0, s>>>(n, b, w, r, P.mask);
+    gs::norms_kernel<<<RB, RT, 0, s>>>(n, r, part, part + RB);
+    gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 3);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hS, S, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    bnorm = std::sqrt(hS[3]);
+  }
+  while (e == cudaSuccess) {
+    // r = b - A x in FP64-accurate arithmetic
+    gs::scatter_kernel<double><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, x, Ul);
+    e = launch_hi(ah);
+    if (e != cudaSuccess) break;
+    gs::gather_kernel<double><<<gs::grid_for(n), 256, 0, s>>>(n, P.off, P.idx, Yl, w, P.mask);
+    gs::residual_kernel<<<gs::grid_for(n), 256, 0, s>>>(n, b, w, r, P.mask);
+    gs::norms_kernel<<<RB, RT, 0, s>>>(n, r, part, part + RB);
+    gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 2);
+    gs::finish_max_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 5);
+    e = cudaMemcpyAsync(hS + 2, S + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    const double rn = std::sqrt(hS[2]);
+    *relres = bnorm > 0.0 ? rn / bnorm : 0.0;
+    if (bnorm == 0.0 || rn <= rtol * bnorm) {
+      *converged = 1;
+      break;
+    }
+    if (!(rn == rn) || *outer >= max_outer) break;
+    // inner solve A d = r / sigma in float32
+    gs::scale_down_kernel<<<gs::grid_for(n), 256, 0, s>>>(n, r, S + 5, r32, d32);
+    int it = 0, conv = 0;
+    double rr = 0.0;
+    e = pcg_core<float>(P, lo, launch_lo, W, r32, d32, inner_rtol, max_inner, &it, &rr, &conv, s);
+    if (e != cudaSuccess) break;
+    *inner_total += it;
+    gs::correct_kernel<<<gs::grid_for(n), 256, 0, s>>>(n, d32, S + 5, x);
+    ++*outer;
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  W.release();
+  cudaFree(r); cudaFree(w); cudaFree(Ul); cudaFree(Yl); cudaFree(r32); cudaFree(d32);
+  cudaFree(S); cudaFree(part); cudaFreeHost(hS);
+  return e;
 }
 
 }  // namespace ax

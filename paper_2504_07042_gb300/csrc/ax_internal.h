@@ -80,8 +80,8 @@ cudaError_t upload_tables_fp32(int device);
 cudaError_t upload_tables_dw(int device);
 cudaError_t upload_tables_setup(int device);
 
-// FP32-pipe instructions per node of the double-word kernel (design count).
-double dw_ops_per_node(int N1, int kind);
+// Binding-pipe instructions per node of the AxLocal kernel (design count).
+double pipe_ops_per_node(int N1, int kind, int prec);
 
 // Setup kernels (FP64, ax_setup.cu).  flags: device int[4] zeroed by the caller:
 //   [0] count of GLL nodes with det J <= 0, [1] count of non-affine elements,
@@ -104,5 +104,9 @@ cudaError_t gs_scatter_run(const GsPlan &p, bool f64, const void *u, void *U, cu
 cudaError_t pcg_run(const GsPlan &P, bool f64, const AxArgs &base, cudaError_t (*launch)(const AxArgs &),
                     const void *b, void *x, const void *diag_global, double rtol, int maxit, int *iters,
                     double *relres, int *converged, cudaStream_t s);
+cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launch_hi)(const AxArgs &),
+                          const AxArgs &lo, cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x,
+                          const float *diag_lo, double rtol, double inner_rtol, int max_outer, int max_inner,
+                          int *outer, int *inner_total, double *relres, int *converged, cudaStream_t s);
 
 }  // namespace ax

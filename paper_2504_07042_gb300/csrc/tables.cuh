@@ -33,6 +33,31 @@ inline bool build_packed_tables(double *D, double *w, double *x) {
   return true;
 }
 
+// Even-odd blocks (see ax_fiber.cuh) of D and of D^T for every order, from
+// the packed D tables.  Block of order N1 at tab_off_D(N1), c = N1/2:
+//   rows i < c: [ (M[i][m]+M[i][N-m])/2 , (M[i][m]-M[i][N-m])/2 (m < c) | M[i][c] if N1 odd ]
+//   row c (N1 odd): M[c][m], m < c.
+inline void build_eo_tables(const double *Dp, double *eoD, double *eoDT) {
+  for (int N1 = 2; N1 <= kMaxN1; ++N1) {
+    const double *D = Dp + tab_off_D(N1);
+    const int c = N1 / 2, N = N1 - 1;
+    for (int t = 0; t < 2; ++t) {
+      double *out = (t == 0 ? eoD : eoDT) + tab_off_D(N1);
+      auto M = [&](int a, int b) { return t == 0 ? D[a * N1 + b] : D[b * N1 + a]; };
+      for (int q = 0; q < N1 * N1; ++q) out[q] = 0.0;
+      for (int i = 0; i < c; ++i) {
+        for (int m = 0; m < c; ++m) {
+          out[i * N1 + m] = 0.5 * (M(i, m) + M(i, N - m));
+          out[i * N1 + c + m] = 0.5 * (M(i, m) - M(i, N - m));
+        }
+        if (N1 & 1) out[i * N1 + 2 * c] = M(i, c);
+      }
+      if (N1 & 1)
+        for (int m = 0; m < c; ++m) out[c * N1 + m] = M(c, m);
+    }
+  }
+}
+
 // Per-device "uploaded" bookkeeping for one translation unit.
 struct UploadOnce {
   std::mutex mu;

@@ -26,6 +26,59 @@ __global__ void k_ffma(double *out, int iters, float b, float c) {
   }
   out[g] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
+// packed FP32 pairs (fma.rn.f32x2 / add.rn.f32x2): two FP32 operations per lane per instruction
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm volatile("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm volatile("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long pk(float x, float y) {
+  return ((unsigned long long)__float_as_uint(y) << 32) | __float_as_uint(x);
+}
+__global__ void k_ffma2(double *out, int iters, float b, float c) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long bb = pk(b, b), cc = pk(c, c);
+  unsigned long long a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = pk(g * 1e-9f + q, g * 1e-9f - q);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = f2fma(a[q], bb, cc);
+  }
+  float s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += __uint_as_float((unsigned)a[q]) + __uint_as_float((unsigned)(a[q] >> 32));
+  out[g] = s;
+}
+__global__ void k_fadd2(double *out, int iters, float c) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long cc = pk(c, -c);
+  unsigned long long a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) a[q] = pk(g * 1e-9f + q, g * 1e-9f - q);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = f2add(a[q], cc);
+  }
+  float s = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += __uint_as_float((unsigned)a[q]) + __uint_as_float((unsigned)(a[q] >> 32));
+  out[g] = s;
+}
+__global__ void k_fadd(double *out, int iters, float c) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  float a0 = g * 1e-9f, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = __fadd_rn(a0, c); a1 = __fadd_rn(a1, c); a2 = __fadd_rn(a2, c); a3 = __fadd_rn(a3, c);
+    a4 = __fadd_rn(a4, c); a5 = __fadd_rn(a5, c); a6 = __fadd_rn(a6, c); a7 = __fadd_rn(a7, c);
+  }
+  out[g] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
 __global__ void k_dmma(double *out, int iters) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   double a = 1.0 + (threadIdx.x & 7) * 1e-3, b = 0.5;
@@ -154,6 +207,12 @@ int main() {
   printf(", \"dfma_tflops\": %.4f", 2.0 * 8 * it * nth / (ms * 1e-3) / 1e12);
   it = 65536; ms = best_ms([&] { k_ffma<<<blocks, threads>>>(out, it, 0.999999f, 1e-7f); }, 3); CK(cudaGetLastError());
   printf(", \"ffma_tflops\": %.3f", 2.0 * 8 * it * nth / (ms * 1e-3) / 1e12);
+  it = 65536; ms = best_ms([&] { k_ffma2<<<blocks, threads>>>(out, it, 0.999999f, 1e-7f); }, 3); CK(cudaGetLastError());
+  printf(", \"ffma2_f32x2_tflops\": %.3f", 2.0 * 16 * it * nth / (ms * 1e-3) / 1e12);
+  it = 65536; ms = best_ms([&] { k_fadd<<<blocks, threads>>>(out, it, 1e-7f); }, 3); CK(cudaGetLastError());
+  printf(", \"fadd_gops\": %.1f", 8.0 * it * nth / (ms * 1e-3) / 1e9);
+  it = 65536; ms = best_ms([&] { k_fadd2<<<blocks, threads>>>(out, it, 1e-7f); }, 3); CK(cudaGetLastError());
+  printf(", \"fadd2_f32x2_gops\": %.1f", 16.0 * it * nth / (ms * 1e-3) / 1e9);
   it = 512; ms = best_ms([&] { k_dmma<<<blocks, threads>>>(out, it); }, 3); CK(cudaGetLastError());
   printf(", \"dmma_m8n8k4_tflops\": %.4f", 512.0 * 4 * it * (nth / 32) / (ms * 1e-3) / 1e12);
   it = 4096; ms = best_ms([&] { k_cvt<<<blocks, threads>>>(out, it); }, 3); CK(cudaGetLastError());
