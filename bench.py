@@ -303,8 +303,10 @@ def run(args):
     del Xh, Yh
 
     sweep = None
+    pcg = None
     if not args.no_sweep and rank == 0:
         sweep = run_sweep(ax, torch, dev, hbm, clocks.get("sm_mhz"))
+        pcg = run_pcg(ax, torch, dev)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -318,12 +320,53 @@ def run(args):
     if rank == 0:
         rate, cores, sample = cpu_oracle_rate()
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if pcg is not None:
+            line["pcg"] = pcg
         if sweep is not None:
             line["sweep"] = sweep
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def run_pcg(ax, torch, dev):
+    """Poisson -lap u = 3 pi^2 u, u = sin(pi x) sin(pi y) sin(pi z), homogeneous
+    Dirichlet, 16^3 perturbed trilinear elements at N = 7: wall time to 1e-8
+    relative residual for FP64-accurate Jacobi-PCG (double-word AxLocal) and
+    for the mixed-precision solver (FP64 refinement, float32 inner PCG)."""
+    from paper_2504_07042_gb300 import inputs
+    N, n = 7, 16
+    V = inputs.box_vertices(n, n, n, perturb=0.1, seed=0)
+    gid, ng = inputs.box_global_ids(n, n, n, N)
+    mask = inputs.box_boundary_mask(n, n, n, N)
+    Vd = torch.from_numpy(V).to(dev)
+    hi = ax.Ax(Vd, N, "trilinear", "f64dw")
+    hi.gs_setup(torch.from_numpy(gid).to(dev), ng, torch.from_numpy(mask).to(dev))
+    lo = ax.Ax(Vd, N, "trilinear", "fp32")
+    XYZ = torch.empty((V.shape[0], 3, (N + 1) ** 3), dtype=torch.float64, device=dev)
+    hi.ax_node_coords(XYZ)
+    u = torch.sin(torch.pi * XYZ[:, 0]) * torch.sin(torch.pi * XYZ[:, 1]) * torch.sin(torch.pi * XYZ[:, 2])
+    b = hi.gs_gather(hi.ax_mass(3 * torch.pi ** 2 * u, torch.empty_like(u)), torch.empty(ng, dtype=torch.float64, device=dev))
+    ug = torch.zeros(ng, dtype=torch.float64, device=dev)
+    ug[torch.from_numpy(gid.reshape(-1)).to(dev)] = u.reshape(-1)
+    out = {"workload": "16^3 perturbed trilinear elements, N=7, %d global nodes, rtol 1e-8" % ng}
+    for name, fn in (("fp64_jacobi_pcg", lambda x: hi.pcg_solve(b, x, rtol=1e-8, maxit=20000, precond=1)),
+                     ("mixed_fp64_refinement_fp32_inner", lambda x: hi.pcg_solve_mixed(lo, b, x, rtol=1e-8,
+                                                                                      inner_rtol=1e-3))):
+        x = torch.zeros(ng, dtype=torch.float64, device=dev)
+        fn(x)  # warm-up (allocations, module loading)
+        x.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = fn(x)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out[name] = {"seconds": dt, "result": list(res), "max_error_vs_exact": float((x - ug).abs().max())}
+    out["speedup_mixed_over_fp64"] = out["fp64_jacobi_pcg"]["seconds"] / out["mixed_fp64_refinement_fp32_inner"]["seconds"]
+    hi.ax_destroy()
+    lo.ax_destroy()
+    return out
 
 
 def run_sweep(ax, torch, dev, hbm, sm_mhz):

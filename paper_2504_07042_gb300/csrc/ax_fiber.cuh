@@ -351,11 +351,14 @@ __global__ void __launch_bounds__(Shape<N1>::threads)
   const typename P::C *cw = c_w + tab_off_v(N1);
   const typename P::C *cx = c_x + tab_off_v(N1);
 
-  // pass 0: the CTA's elements (contiguous in HBM) into padded shared memory
-  for (int m = tid; m < nel * n3; m += Sh::threads) {
-    const int ze = m / n3, l = m % n3;
-    const int i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
-    xs[ze * ES + Sh::at(i, j, k)] = P::st(P::from_io(X[e0 * n3 + m]));
+  // pass 0: the CTA's elements (contiguous in HBM) into padded shared memory,
+  // one i-row of N1 values per thread and step (row = j + N1 (k + N1 z) is
+  // also the padded row index: padded offset = row * P)
+  for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
+    const typename P::IO *src = X + e0 * n3 + (int64_t)row * N1;
+    S *dst = xs + row * Sh::P;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) dst[i] = P::st(P::from_io(src[i]));
   }
   if constexpr (GW > 0) {
     for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
@@ -448,10 +451,11 @@ __global__ void __launch_bounds__(Shape<N1>::threads)
   __syncthreads();
 
   // pass 5: Y to HBM
-  for (int m = tid; m < nel * n3; m += Sh::threads) {
-    const int ze = m / n3, l = m % n3;
-    const int i = l % N1, j = (l / N1) % N1, k = l / (N1 * N1);
-    Y[e0 * n3 + m] = P::to_io(P::ld(xs + ze * ES + Sh::at(i, j, k)));
+  for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
+    typename P::IO *dst = Y + e0 * n3 + (int64_t)row * N1;
+    const S *src = xs + row * Sh::P;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) dst[i] = P::to_io(P::ld(src + i));
   }
 }
 

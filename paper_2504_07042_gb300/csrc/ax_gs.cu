@@ -91,52 +91,94 @@ __global__ void __launch_bounds__(kRedThreads)
     gather_dot_kernel(int64_t n_global, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
                       const T *__restrict__ Y, T *__restrict__ w, const uint8_t *__restrict__ mask,
                       const T *__restrict__ p, double *__restrict__ partial) {
-  double d = 0.0;
+  T d = T(0);
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
     T s = T(0);
     for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
     if (mask && mask[g]) s = T(0);
     w[g] = s;
-    d += (double)p[g] * (double)s;
+    d += p[g] * s;
   }
-  block_reduce_store(d, partial + blockIdx.x);
+  block_reduce_store((double)d, partial + blockIdx.x);
 }
 
-// Scalars S: [0] rz, [1] pw, [2] rr, [3] bb, [4] rz_new
+// Scalars S: [0] rz, [1] pw, [2] rr, [3] bb, [4] rz_new, [5] sigma (mixed
+// precision), [6] done flag, [7] iteration at which the test was met
+// (negative: NaN), [8] tol^2 = rtol^2 bb, [9] iterations issued,
+// [10] alpha, [11] beta.  alpha and beta are divided once per iteration by
+// one thread: FP64 division is a long sequence on GB300's slow FP64 pipe.
+// Vector kernels accumulate their partial dot products in their own type T
+// (no float -> double conversions per element on the FP64 pipe).
+// Once done is set, the update kernels return at once, so iterations queued
+// after convergence leave x unchanged (the host checks every few iterations).
+constexpr int kScalars = 16;
 // x += alpha p; r -= alpha w; z = r * inv_diag (0 on masked); partials of r.z and r.r
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
     update_kernel(int64_t n, const double *__restrict__ S, const T *__restrict__ p, const T *__restrict__ w,
                   T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, const T *__restrict__ inv_diag,
                   const uint8_t *__restrict__ mask, double *__restrict__ part_rz, double *__restrict__ part_rr) {
-  const double alpha = S[0] / S[1];
-  double rz = 0.0, rr = 0.0;
+  if (S[6] != 0.0) return;
+  const T alpha = (T)S[10];
+  T rz = T(0), rr = T(0);
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const T xg = x[g] + (T)alpha * p[g];
-    const T rg = r[g] - (T)alpha * w[g];
+    const T xg = x[g] + alpha * p[g];
+    const T rg = r[g] - alpha * w[g];
     T zg = inv_diag ? rg * inv_diag[g] : rg;
     if (mask && mask[g]) zg = T(0);
     x[g] = xg;
     r[g] = rg;
     z[g] = zg;
-    rz += (double)rg * (double)zg;
-    rr += (double)rg * (double)rg;
+    rz += rg * zg;
+    rr += rg * rg;
   }
-  block_reduce_store(rz, part_rz + blockIdx.x);
+  block_reduce_store((double)rz, part_rz + blockIdx.x);
   __syncthreads();
-  block_reduce_store(rr, part_rr + blockIdx.x);
+  block_reduce_store((double)rr, part_rr + blockIdx.x);
 }
 
 // p = z + beta p, beta = rz_new / rz; the last block to finish moves rz_new into rz
 template <typename T>
 __global__ void direction_kernel(int64_t n, const double *__restrict__ S, const T *__restrict__ z,
                                  T *__restrict__ p) {
-  const double beta = S[4] / S[0];
+  if (S[6] != 0.0) return;
+  const T beta = (T)S[11];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    p[g] = z[g] + (T)beta * p[g];
+    p[g] = z[g] + beta * p[g];
 }
 
-__global__ void shift_kernel(double *S) { S[0] = S[4]; }
+__global__ void shift_kernel(double *S) {
+  if (S[6] == 0.0) S[0] = S[4];
+}
+
+// one block: S[1] = sum of partials (p . A p), then alpha = rz / (p . A p)
+__global__ void __launch_bounds__(kRedThreads) finish_alpha_kernel(const double *__restrict__ partial, int nb,
+                                                                   double *__restrict__ S) {
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) s += partial[q];
+  block_reduce_store(s, S + 1);
+  __syncthreads();
+  if (threadIdx.x == 0) S[10] = S[1] != 0.0 ? S[0] / S[1] : 0.0;
+}
+
+// one thread: count the iteration, test convergence (||r||^2 <= tol^2) or NaN,
+// beta = rz_new / rz
+__global__ void check_kernel(double *S) {
+  if (S[6] != 0.0) return;
+  S[11] = S[0] != 0.0 ? S[4] / S[0] : 0.0;
+  const double it = S[9] + 1.0;
+  S[9] = it;
+  const double rr = S[2];
+  if (rr <= S[8]) {
+    S[6] = 1.0;
+    S[7] = it;
+  } else if (!(rr == rr)) {
+    S[6] = 1.0;
+    S[7] = -it;
+  }
+}
+
+__global__ void set_kernel(double *S, int idx, double v) { S[idx] = v; }
 
 // initial: r = b - w (masked), z = r * inv_diag, p = z; partials of r.z, r.r, b.b
 template <typename T>
@@ -144,7 +186,7 @@ __global__ void __launch_bounds__(kRedThreads)
     init_kernel(int64_t n, const T *__restrict__ b, const T *__restrict__ w, T *__restrict__ r, T *__restrict__ z,
                 T *__restrict__ p, const T *__restrict__ inv_diag, const uint8_t *__restrict__ mask,
                 double *__restrict__ part_rz, double *__restrict__ part_rr, double *__restrict__ part_bb) {
-  double rz = 0.0, rr = 0.0, bb = 0.0;
+  T rz = T(0), rr = T(0), bb = T(0);
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     const bool m = mask && mask[g];
     const T bg = m ? T(0) : b[g];
@@ -153,15 +195,15 @@ __global__ void __launch_bounds__(kRedThreads)
     r[g] = rg;
     z[g] = zg;
     p[g] = zg;
-    rz += (double)rg * (double)zg;
-    rr += (double)rg * (double)rg;
-    bb += (double)bg * (double)bg;
+    rz += rg * zg;
+    rr += rg * rg;
+    bb += bg * bg;
   }
-  block_reduce_store(rz, part_rz + blockIdx.x);
+  block_reduce_store((double)rz, part_rz + blockIdx.x);
   __syncthreads();
-  block_reduce_store(rr, part_rr + blockIdx.x);
+  block_reduce_store((double)rr, part_rr + blockIdx.x);
   __syncthreads();
-  block_reduce_store(bb, part_bb + blockIdx.x);
+  block_reduce_store((double)bb, part_bb + blockIdx.x);
 }
 
 template <typename T>
@@ -282,9 +324,10 @@ struct PcgWork {
     if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(T) * nl);
     if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(T) * nl);
     if (e == cudaSuccess && jacobi) e = cudaMalloc(&inv, sizeof(T) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * gs::kScalars);
+    if (e == cudaSuccess) e = cudaMemset(S, 0, sizeof(double) * gs::kScalars);
     if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 3 * gs::kRedBlocks);
-    if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * gs::kScalars);
     return e;
   }
   void release() {
@@ -319,7 +362,7 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
   gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 0);
   gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
   gs::finish_kernel<<<1, RT, 0, s>>>(part + 2 * RB, RB, S + 3);
-  e = cudaMemcpyAsync(hS, S, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(hS, S, sizeof(double) * gs::kScalars, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
   const double bnorm = std::sqrt(hS[3]);
@@ -328,27 +371,41 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
   if (bnorm == 0.0 || rnorm <= rtol * bnorm) {
     *converged = 1;
   } else {
-    while (it < maxit) {
-      gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, W.p, W.Ul);
-      e = launch(a);
-      if (e != cudaSuccess) return e;
-      gs::gather_dot_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask, W.p, part);
-      gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 1);
-      gs::update_kernel<T><<<RB, RT, 0, s>>>(n, S, W.p, W.w, x, W.r, W.z, W.inv, P.mask, part, part + RB);
-      gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 4);
-      gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
-      e = cudaMemcpyAsync(hS + 2, S + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+    gs::set_kernel<<<1, 1, 0, s>>>(S, 8, rtol * rtol * hS[3]);
+    gs::set_kernel<<<1, 1, 0, s>>>(S, 6, 0.0);
+    gs::set_kernel<<<1, 1, 0, s>>>(S, 9, 0.0);
+    constexpr int kCheck = 16;  // iterations queued between host checks
+    int issued = 0;
+    while (issued < maxit) {
+      const int block = (maxit - issued) < kCheck ? (maxit - issued) : kCheck;
+      for (int q = 0; q < block; ++q) {
+        gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, W.p, W.Ul);
+        e = launch(a);
+        if (e != cudaSuccess) return e;
+        gs::gather_dot_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask, W.p, part);
+        gs::finish_alpha_kernel<<<1, RT, 0, s>>>(part, RB, S);
+        gs::update_kernel<T><<<RB, RT, 0, s>>>(n, S, W.p, W.w, x, W.r, W.z, W.inv, P.mask, part, part + RB);
+        gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 4);
+        gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
+        gs::check_kernel<<<1, 1, 0, s>>>(S);
+        gs::direction_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, S, W.z, W.p);
+        gs::shift_kernel<<<1, 1, 0, s>>>(S);
+      }
+      issued += block;
+      e = cudaMemcpyAsync(hS, S, sizeof(double) * gs::kScalars, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return e;
-      ++it;
       rnorm = std::sqrt(hS[2]);
-      if (!(rnorm == rnorm)) break;  // NaN: reported as not converged
-      if (rnorm <= rtol * bnorm) {
-        *converged = 1;
+      if (hS[6] != 0.0) {
+        if (hS[7] > 0.0) {
+          *converged = 1;
+          it = (int)hS[7];
+        } else {
+          it = (int)(-hS[7]);
+        }
         break;
       }
-      gs::direction_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, S, W.z, W.p);
-      gs::shift_kernel<<<1, 1, 0, s>>>(S);
+      it = issued;
     }
   }
   *iters = it;
@@ -464,9 +521,9 @@ cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launc
   if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(double) * nl);
   if (e == cudaSuccess) e = cudaMalloc(&r32, sizeof(float) * n);
   if (e == cudaSuccess) e = cudaMalloc(&d32, sizeof(float) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * gs::kScalars);
   if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 2 * RB);
-  if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * gs::kScalars);
   if (e == cudaSuccess && diag_lo)
     gs::invert_kernel<float><<<gs::grid_for(n), 256, 0, s>>>(n, diag_lo, W.inv, P.mask);
   AxArgs ah = hi;
@@ -481,7 +538,7 @@ cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launc
     gs::residual_kernel<<<gs::grid_for(n), 256, 0, s>>>(n, b, w, r, P.mask);
     gs::norms_kernel<<<RB, RT, 0, s>>>(n, r, part, part + RB);
     gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 3);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hS, S, sizeof(double) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hS, S, sizeof(double) * gs::kScalars, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     bnorm = std::sqrt(hS[3]);
   }

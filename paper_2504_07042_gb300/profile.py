@@ -25,7 +25,11 @@ def main():
     ap.add_argument("--mesh", default="trilinear", choices=["trilinear", "parallelepiped"])
     ap.add_argument("--box", type=int, nargs=3, default=[32, 32, 32])
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--pcg", type=int, default=0, help="instead: run this many Jacobi-PCG iterations on the box")
+    ap.add_argument("--mixed", action="store_true", help="with --pcg: the mixed-precision solver (float32 inner)")
     a = ap.parse_args()
+    if a.pcg:
+        return run_pcg(a)
     ex, ey, ez = a.box
     V = inputs.parallelepiped_vertices(ex, ey, ez) if a.mesh == "parallelepiped" else \
         inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
@@ -45,6 +49,41 @@ def main():
     info = op.ax_query()
     print(json.dumps({"E": op.E, "N": a.N, "kind": a.kind, "prec": a.prec, "ms": times,
                       "gdofs": [op.E * op.n3 / (t * 1e-3) / 1e9 for t in times], "info": info}))
+
+
+def run_pcg(a):
+    """-lap u = 3 pi^2 u on the box mesh, homogeneous Dirichlet, --pcg iterations."""
+    import time
+
+    import torch
+
+    from paper_2504_07042_gb300 import ax, inputs
+
+    ex, ey, ez = a.box
+    N = a.N
+    V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    gid, ng = inputs.box_global_ids(ex, ey, ez, N)
+    mask = inputs.box_boundary_mask(ex, ey, ez, N)
+    dev = torch.device("cuda:0")
+    Vd = torch.from_numpy(V).to(dev)
+    op = ax.Ax(Vd, N, a.kind, a.prec)
+    op.gs_setup(torch.from_numpy(gid).to(dev), ng, torch.from_numpy(mask).to(dev))
+    XYZ = torch.empty((V.shape[0], 3, (N + 1) ** 3), dtype=torch.float64, device=dev)
+    op.ax_node_coords(XYZ)
+    u = torch.sin(torch.pi * XYZ[:, 0]) * torch.sin(torch.pi * XYZ[:, 1]) * torch.sin(torch.pi * XYZ[:, 2])
+    f = (3 * torch.pi ** 2 * u).to(op.dtype)
+    b = op.gs_gather(op.ax_mass(f, torch.empty_like(f)), torch.empty(ng, dtype=op.dtype, device=dev))
+    x = torch.zeros(ng, dtype=op.dtype, device=dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    if a.mixed:
+        lo = ax.Ax(Vd, N, a.kind, "fp32")
+        res = op.pcg_solve_mixed(lo, b, x, rtol=1e-30, inner_rtol=1e-3, max_outer=1, max_inner=a.pcg)
+    else:
+        res = op.pcg_solve(b, x, rtol=1e-30, maxit=a.pcg, precond=1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    print(json.dumps({"E": op.E, "N": N, "n_global": ng, "result": list(res), "seconds": dt}))
 
 
 if __name__ == "__main__":
