@@ -138,6 +138,22 @@ def _time_launches(torch, fn, steps, warmup, stream):
     return t0.elapsed_time(t1) / steps  # ms
 
 
+def reduce_max_ms(torch, ms, device):
+    """Max over ranks of a per-rank time (ms); identity on one process."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, dofs_per_rank, ms_max):
+    """Replicas: every rank processes dofs_per_rank local DOFs per step; the
+    job's throughput is all ranks' DOFs over the slowest rank's time (GDOF/s)."""
+    return world * dofs_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def _pipe_peak(info, sm_mhz):
     clk = (sm_mhz or 1980.0) * 1e6
     if info["pipe"] == 0:
@@ -268,13 +284,9 @@ def run(args):
             fn()
         t1.record(stream)
         torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = reduce_max_ms(torch, t0.elapsed_time(t1) / args.steps, dev)
     clocks = ck.summary()
-    value = world * E * n3 / (ms * 1e-3) / 1e9
+    value = whole_job_value(world, E * n3, ms)
     roof = _roofline(info, ms, clocks.get("sm_mhz"), hbm)
     src = _src_hash()
     kname = "ax_dw_kernel<8,%d>" % info["kind"]
@@ -304,9 +316,11 @@ def run(args):
 
     sweep = None
     pcg = None
+    batch = None
     if not args.no_sweep and rank == 0:
         sweep = run_sweep(ax, torch, dev, hbm, clocks.get("sm_mhz"))
         pcg = run_pcg(ax, torch, dev)
+        batch = run_batch(ax, torch, dev)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -322,6 +336,8 @@ def run(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
         if pcg is not None:
             line["pcg"] = pcg
+        if batch is not None:
+            line["batch"] = batch
         if sweep is not None:
             line["sweep"] = sweep
         print(json.dumps(line), flush=True)
@@ -366,6 +382,63 @@ def run_pcg(ax, torch, dev):
     out["speedup_mixed_over_fp64"] = out["fp64_jacobi_pcg"]["seconds"] / out["mixed_fp64_refinement_fp32_inner"]["seconds"]
     hi.ax_destroy()
     lo.ax_destroy()
+    return out
+
+
+def run_batch(ax, torch, dev):
+    """64 perturbed-box meshes, E log-uniform on [64, 4096] (near-cubic boxes),
+    N uniform on {3,5,7,9}, FP32, trilinear recompute: batched AxLocal (one
+    launch per order) and batched Jacobi-PCG (one CUDA-graph launch per CG
+    iteration) against the per-mesh paths (one launch per mesh per step)."""
+    from paper_2504_07042_gb300 import inputs
+    spec = inputs.batch_meshes()
+    meshes = []
+    for s, (ex, ey, ez, N) in enumerate(spec):
+        V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=s)
+        gid, ng = inputs.box_global_ids(ex, ey, ez, N)
+        mask = inputs.box_boundary_mask(ex, ey, ez, N)
+        meshes.append((torch.from_numpy(V).to(dev), N, torch.from_numpy(gid).to(dev), ng,
+                       torch.from_numpy(mask).to(dev)))
+    bt = ax.AxBatch(meshes, "trilinear", "fp32")
+    per = [ax.Ax(m[0], m[1], "trilinear", "fp32") for m in meshes]
+    stream = torch.cuda.current_stream()
+    X = torch.rand(bt.n_local, device=dev, dtype=torch.float32) * 2 - 1
+    Y = torch.empty_like(X)
+    slices = []
+    for m, op in enumerate(per):
+        n = op.E * op.n3
+        lo = bt.local_offsets[m]
+        slices.append((op, X[lo:lo + n], Y[lo:lo + n]))
+
+    def per_mesh():
+        for op, xs, ys in slices:
+            op.ax_local(xs, ys, stream)
+
+    untuned = _time_launches(torch, lambda: bt.ax_batch_local(X, Y, stream), 10, 3, stream)
+    tune = bt.ax_batch_tune()
+    batched = _time_launches(torch, lambda: bt.ax_batch_local(X, Y, stream), 10, 3, stream)
+    single = _time_launches(torch, per_mesh, 10, 3, stream)
+    out = {"meshes": len(spec), "elements": int(sum(m[0].shape[0] for m in meshes)), "local_dofs": bt.n_local,
+           "global_dofs": bt.n_global, "orders": sorted(set(int(m[1]) for m in meshes)),
+           "tuned_tile_grid_per_order": {str(k): list(v) for k, v in tune.items()},
+           "axlocal_batched_ms": batched, "axlocal_batched_untuned_ms": untuned, "axlocal_per_mesh_ms": single,
+           "axlocal_batched_gdofs": bt.n_local / (batched * 1e-3) / 1e9,
+           "axlocal_per_mesh_gdofs": bt.n_local / (single * 1e-3) / 1e9}
+    bvec = torch.ones(bt.n_global, device=dev, dtype=torch.float32)
+    for graph, name in ((1, "pcg_graph"), (0, "pcg_per_mesh")):
+        x = torch.zeros_like(bvec)
+        bt.ax_batch_pcg(bvec, x, rtol=1e-5, maxit=20000, graph=graph)  # warm-up
+        x.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        it, rr, st = bt.ax_batch_pcg(bvec, x, rtol=1e-5, maxit=20000, graph=graph)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t, "status": st, "max_iterations": max(it),
+                     "total_iterations": sum(it), "max_relres": max(rr)}
+    out["pcg_speedup_graph_over_per_mesh"] = out["pcg_per_mesh"]["seconds"] / out["pcg_graph"]["seconds"]
+    for op in per:
+        op.ax_destroy()
+    bt.ax_batch_destroy()
     return out
 
 

@@ -179,6 +179,61 @@ ax_status pcg_solve_mixed(ax_ctx *hi, ax_ctx *lo, const double *b_global, double
                           double inner_rtol, int max_outer, int max_inner, int *outer_iters, int *inner_iters,
                           double *relres, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent meshes of uneven size and order.
+ * Meshes are grouped by order N; each group runs as one AxLocal launch over
+ * the union of its elements.  The batch's local vector concatenates the
+ * groups' local vectors (group by increasing first appearance of N, meshes
+ * in batch order inside a group); the batch's global vector concatenates the
+ * meshes' global vectors in batch order (ax_batch_sizes gives the offsets).
+ * ---------------------------------------------------------------------- */
+typedef struct ax_batch ax_batch;
+
+/* B meshes; mesh m: E[m] elements of order N[m], vertices[m] (device
+ * [E][8][3] float64), global_id[m] (device [E][n3] int64, numbering local to
+ * the mesh), n_global[m], mask[m] (device uint8 [n_global] or NULL; mask may
+ * be NULL).  All meshes share kind and prec.  Also builds one per-mesh
+ * context for each mesh (the per-mesh reference path of ax_batch_pcg).
+ * Synchronises. */
+ax_status ax_batch_setup(ax_batch **out, int B, const int64_t *E, const int *N, const double *const *vertices,
+                         const int64_t *const *global_id, const int64_t *n_global, const uint8_t *const *mask,
+                         ax_geom_kind kind, ax_precision prec, void *stream);
+
+/* Sizes of the batch vectors and the per-mesh offsets (host arrays of B and
+ * B+1 entries; any pointer may be NULL). */
+ax_status ax_batch_sizes(const ax_batch *b, int64_t *n_local, int64_t *n_global, int64_t *local_offsets,
+                         int64_t *global_offsets);
+
+/* AxLocal of every mesh: X, Y device batch local vectors.  One launch per
+ * distinct order. */
+ax_status ax_batch_local(ax_batch *b, const void *X, void *Y, void *stream);
+
+/* Autotune, per group (order, geometry kind), the tile (elements per CTA:
+ * 0 = base, 1 = twice, FP32 only) and the grid (0 = one CTA per element
+ * block, else a persistent grid of k * SMs CTAs) by timing the group's
+ * AxLocal; the choice is kept by the batch.  tiles, grids: host arrays with
+ * one entry per group (or NULL).  Synchronises. */
+ax_status ax_batch_tune(ax_batch *b, int *tiles, int64_t *grids, void *stream);
+
+/* Independent Jacobi-PCG solves of every mesh's Dirichlet Poisson system.
+ *   b_global, x_global: device batch global vectors (x: initial guess in,
+ *   solutions out).  Per-mesh stop at ||r|| <= rtol ||b||.
+ *   graph = 1: all meshes advance together; one CG iteration of the whole
+ *   batch is captured once as a CUDA graph and launched once per iteration
+ *   (per-mesh scalars, segmented reductions, converged meshes idle).
+ *   graph = 0: reference path, each mesh solved in turn with its own
+ *   launches (pcg_solve on its per-mesh context).
+ *   iters, relres: host arrays [B].  AX_ENOTCONV if a mesh hit maxit.
+ * Synchronises. */
+ax_status ax_batch_pcg(ax_batch *b, const void *b_global, void *x_global, double rtol, int maxit, int graph,
+                       int *iters, double *relres, void *stream);
+
+/* Message of the batch's last failed call (or of batch creation when b is NULL). */
+const char *ax_batch_last_error(const ax_batch *b);
+
+/* Release the batch (NULL accepted). */
+void ax_batch_destroy(ax_batch *b);
+
 /* Algorithmic cost of one ax_local call (per element): bytes moved to and
  * from HBM by the kernel's design, the paper's effective flops
  * F_ax = 12 N1^4 + 15 N1^3 (Table 2), and the arithmetic instructions the

@@ -62,6 +62,23 @@ _lib.pcg_solve.restype = _int
 _lib.pcg_solve_mixed.argtypes = [_vp, _vp, _vp, _vp, _dbl, _dbl, _int, _int, ctypes.POINTER(_int),
                                   ctypes.POINTER(_int), ctypes.POINTER(_dbl), _vp]
 _lib.pcg_solve_mixed.restype = _int
+_lib.ax_batch_setup.argtypes = [ctypes.POINTER(_vp), _int, ctypes.POINTER(_i64), ctypes.POINTER(_int),
+                                ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_vp),
+                                _int, _int, _vp]
+_lib.ax_batch_setup.restype = _int
+_lib.ax_batch_sizes.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                ctypes.POINTER(_i64)]
+_lib.ax_batch_sizes.restype = _int
+_lib.ax_batch_local.argtypes = [_vp, _vp, _vp, _vp]
+_lib.ax_batch_local.restype = _int
+_lib.ax_batch_tune.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64), _vp]
+_lib.ax_batch_tune.restype = _int
+_lib.ax_batch_pcg.argtypes = [_vp, _vp, _vp, _dbl, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_dbl), _vp]
+_lib.ax_batch_pcg.restype = _int
+_lib.ax_batch_last_error.argtypes = [_vp]
+_lib.ax_batch_last_error.restype = ctypes.c_char_p
+_lib.ax_batch_destroy.argtypes = [_vp]
+_lib.ax_batch_destroy.restype = None
 _lib.ax_query.argtypes = [_vp, ctypes.POINTER(ax_info)]
 _lib.ax_query.restype = _int
 _lib.ax_last_error.argtypes = [_vp]
@@ -73,6 +90,8 @@ _lib.ax_destroy.restype = None
 
 EXPORTS = ("ax_setup", "ax_local", "ax_local_host", "ax_local_host_static", "ax_factors", "ax_node_coords", "ax_query",
            "gs_setup", "gs_assemble", "gs_gather", "gs_scatter", "ax_mass", "ax_diag", "pcg_solve", "pcg_solve_mixed",
+           "ax_batch_setup", "ax_batch_sizes", "ax_batch_local", "ax_batch_tune", "ax_batch_pcg",
+           "ax_batch_last_error", "ax_batch_destroy",
            "ax_last_error", "ax_status_string", "ax_destroy")
 
 
@@ -208,3 +227,67 @@ class Ax:
 
 def ax_setup(vertices, N, kind="trilinear", prec="fp64", stream=None) -> Ax:
     return Ax(vertices, N, kind, prec, stream)
+
+
+def _bcheck(st: int, b=None):
+    if st != AX_OK:
+        raise AxError(st, _lib.ax_batch_last_error(b).decode())
+
+
+class AxBatch:
+    """Owns an ax_batch: many meshes of uneven size and order.  Method names follow the C ABI."""
+
+    def __init__(self, meshes, kind="trilinear", prec="fp32", stream=None):
+        """meshes: list of (vertices [E][8][3] float64 CUDA tensor, N, global_id [E][n3] int64 CUDA
+        tensor, n_global, mask uint8 CUDA tensor or None)."""
+        kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+        B = len(meshes)
+        self._keep = [m for m in meshes]  # keep the tensors alive during setup
+        E = (_i64 * B)(*[int(m[0].shape[0]) for m in meshes])
+        Ns = (_int * B)(*[int(m[1]) for m in meshes])
+        V = (_vp * B)(*[_ptr(m[0].contiguous()) for m in meshes])
+        G = (_vp * B)(*[_ptr(m[2].contiguous()) for m in meshes])
+        NG = (_i64 * B)(*[int(m[3]) for m in meshes])
+        M = (_vp * B)(*[_ptr(m[4]) if m[4] is not None else None for m in meshes])
+        self.b = _vp()
+        _bcheck(_lib.ax_batch_setup(ctypes.byref(self.b), B, E, Ns, V, G, NG, M, kind, prec, _stream(stream)))
+        self.B, self.prec = B, prec
+        nl, ng = _i64(0), _i64(0)
+        lo, go = (_i64 * B)(), (_i64 * (B + 1))()
+        _bcheck(_lib.ax_batch_sizes(self.b, ctypes.byref(nl), ctypes.byref(ng), lo, go), self.b)
+        self.n_local, self.n_global = nl.value, ng.value
+        self.local_offsets, self.global_offsets = list(lo), list(go)
+        import torch
+        self.dtype = torch.float64 if prec in (AX_FP64, AX_F64DW) else torch.float32
+        self.groups = sorted(set(int(m[1]) for m in meshes), key=[int(m[1]) for m in meshes].index)
+        self._keep = None
+
+    def ax_batch_local(self, X, Y, stream=None):
+        _bcheck(_lib.ax_batch_local(self.b, _ptr(X), _ptr(Y), _stream(stream)), self.b)
+        return Y
+
+    def ax_batch_tune(self, stream=None):
+        n = len(self.groups)
+        tiles, grids = (_int * n)(), (_i64 * n)()
+        _bcheck(_lib.ax_batch_tune(self.b, tiles, grids, _stream(stream)), self.b)
+        return {N: (tiles[i], grids[i]) for i, N in enumerate(self.groups)}
+
+    def ax_batch_pcg(self, b_global, x_global, rtol=1e-8, maxit=10000, graph=1, stream=None, check=True):
+        it, rr = (_int * self.B)(), (_dbl * self.B)()
+        st = _lib.ax_batch_pcg(self.b, _ptr(b_global), _ptr(x_global), float(rtol), int(maxit), int(graph), it, rr,
+                               _stream(stream))
+        if check and st not in (AX_OK, AX_ENOTCONV):
+            _bcheck(st, self.b)
+        return list(it), list(rr), st
+
+    def ax_batch_destroy(self):
+        if self.b:
+            _lib.ax_batch_destroy(self.b)
+            self.b = _vp()
+
+    def __del__(self):
+        try:
+            self.ax_batch_destroy()
+        except Exception:
+            pass

@@ -83,6 +83,12 @@ bool same_device(ax_ctx *c) {
 
 }  // namespace
 
+namespace ax {
+AxArgs ax_ctx_args(const ax_ctx *c) { return make_args(const_cast<ax_ctx *>(c), nullptr, nullptr, nullptr); }
+const Ctx &ax_ctx_core(const ax_ctx *c) { return c->c; }
+const double *ax_ctx_vertices(const ax_ctx *c) { return c->vtx; }
+}  // namespace ax
+
 extern "C" {
 
 const char *ax_status_string(ax_status s) {

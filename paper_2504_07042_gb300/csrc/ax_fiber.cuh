@@ -43,6 +43,7 @@ struct Native {
   using C = T;   // constant-table word
   using IO = T;  // X, Y in HBM
   static constexpr bool kRoll = false;  // short code: unroll the phase and k loops
+  static constexpr int kTiles = sizeof(T) == 4 ? 2 : 1;  // tile variants the autotuner may pick
   __device__ static __forceinline__ V ld(const S *p) { return *p; }
   __device__ static __forceinline__ S st(V v) { return v; }
   __device__ static __forceinline__ V cst(const C *p) { return *p; }
@@ -71,6 +72,7 @@ struct DW {
   using C = float2;
   using IO = double;
   static constexpr bool kRoll = true;  // long code: keep the phase and k loops rolled (instruction cache)
+  static constexpr int kTiles = 1;
   __device__ static __forceinline__ V ld(const S *p) { return dw::from_float2(*p); }
   __device__ static __forceinline__ S st(V v) { return make_float2(v.hi, v.lo); }
   __device__ static __forceinline__ V cst(const C *p) { return dw::from_float2(*p); }
@@ -147,11 +149,11 @@ __device__ __forceinline__ void contract(const typename P::C *__restrict__ eo, c
   }
 }
 
-template <int N1>
+template <int N1, int EM = 1>
 struct Shape {
   static constexpr int n3 = N1 * N1 * N1;
   static constexpr int F = N1 * N1;  // fibers (threads) per element
-  static constexpr int EPB = (F >= 128) ? 1 : (128 / F);
+  static constexpr int EPB = EM * ((F >= 128) ? 1 : (128 / F));  // elements per CTA (EM: tile variant)
   static constexpr int threads = F * EPB;
   static constexpr int P = N1 + 1;            // padded row
   static constexpr int ES = N1 * N1 * P;      // padded element size (words)
@@ -324,11 +326,11 @@ struct GeoWords {
 // the kernel.  Tables (per translation unit, constant memory):
 //   c_eoD / c_eoDT: even-odd blocks of D and D^T, c_w, c_x: weights, points.
 // ---------------------------------------------------------------------------
-template <class P, int N1, int KIND>
-__global__ void __launch_bounds__(Shape<N1>::threads)
+template <class P, int N1, int KIND, int EM>
+__global__ void __launch_bounds__(Shape<N1, EM>::threads)
     ax_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
                     const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y) {
-  using Sh = Shape<N1>;
+  using Sh = Shape<N1, EM>;
   using V = typename P::V;
   using S = typename P::S;
   constexpr int n3 = Sh::n3, EPB = Sh::EPB, ES = Sh::ES;
@@ -342,14 +344,18 @@ __global__ void __launch_bounds__(Shape<N1>::threads)
   const int tid = threadIdx.x;
   const int z = tid / Sh::F, q = tid % Sh::F;
   const int qa = q % N1, qb = q / N1;
-  const int64_t e0 = (int64_t)blockIdx.x * EPB;
-  const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
-  const int64_t e = e0 + z;
-  const bool live = z < nel;
   const typename P::C *eoD = c_eoD + tab_off_D(N1);
   const typename P::C *eoDT = c_eoDT + tab_off_D(N1);
   const typename P::C *cw = c_w + tab_off_v(N1);
   const typename P::C *cx = c_x + tab_off_v(N1);
+  const int64_t nblk = (E + EPB - 1) / EPB;
+
+  // persistent over blocks of EPB elements (one block per CTA when gridDim covers nblk)
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+  const int64_t e0 = blk * EPB;
+  const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+  const int64_t e = e0 + z;
+  const bool live = z < nel;
 
   // pass 0: the CTA's elements (contiguous in HBM) into padded shared memory,
   // one i-row of N1 values per thread and step (row = j + N1 (k + N1 z) is
@@ -457,6 +463,8 @@ __global__ void __launch_bounds__(Shape<N1>::threads)
 #pragma unroll
     for (int i = 0; i < N1; ++i) dst[i] = P::to_io(P::ld(src + i));
   }
+  __syncthreads();  // the next block reuses the shared buffers
+  }
 }
 
 // Factor export through the same geometry code: G_out [E][7][n3] float64.
@@ -495,29 +503,42 @@ __global__ void __launch_bounds__(Shape<N1>::threads)
   }
 }
 
+template <class P, int N1, int KIND, int EM>
+cudaError_t launch_ax_em(const AxArgs &a) {
+  using Sh = Shape<N1, EM>;
+  const int64_t nblk = (a.E + Sh::EPB - 1) / Sh::EPB;
+  if (nblk <= 0) return cudaSuccess;
+  int64_t grid = a.grid > 0 && a.grid < nblk ? a.grid : nblk;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)3 * Sh::EPB * Sh::ES * sizeof(typename P::S);
+  static bool attr_set = false;  // per instantiation; setting the attribute twice is harmless
+  if (!attr_set && smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(ax_fiber_kernel<P, N1, KIND, EM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  ax_fiber_kernel<P, N1, KIND, EM><<<(unsigned)grid, Sh::threads, smem, a.stream>>>(
+      a.E, (const typename P::S *)a.geo, (const typename P::S *)a.lam, (const typename P::IO *)a.X,
+      (typename P::IO *)a.Y);
+  return cudaGetLastError();
+}
+
 template <class P, int N1, int KIND>
 cudaError_t launch_fiber_n(const AxArgs &a, double *G_out) {
   using Sh = Shape<N1>;
-  const int64_t blocks = (a.E + Sh::EPB - 1) / Sh::EPB;
-  if (blocks <= 0) return cudaSuccess;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (G_out) {
+    const int64_t blocks = (a.E + Sh::EPB - 1) / Sh::EPB;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     factors_fiber_kernel<P, N1, KIND><<<(unsigned)blocks, Sh::threads, 0, a.stream>>>(
         a.E, (const typename P::S *)a.geo, (const typename P::S *)a.lam, G_out);
     return cudaGetLastError();
   }
-  const size_t smem = (size_t)3 * Sh::EPB * Sh::ES * sizeof(typename P::S);
-  static bool attr_set = false;  // per instantiation; setting the attribute twice is harmless
-  if (!attr_set && smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(ax_fiber_kernel<P, N1, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  if constexpr (P::kTiles > 1) {
+    if (a.tile == 1) return launch_ax_em<P, N1, KIND, 2>(a);
   }
-  ax_fiber_kernel<P, N1, KIND><<<(unsigned)blocks, Sh::threads, smem, a.stream>>>(
-      a.E, (const typename P::S *)a.geo, (const typename P::S *)a.lam, (const typename P::IO *)a.X,
-      (typename P::IO *)a.Y);
-  return cudaGetLastError();
+  return launch_ax_em<P, N1, KIND, 1>(a);
 }
 
 template <class P, int N1>

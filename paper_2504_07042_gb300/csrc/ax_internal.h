@@ -54,14 +54,16 @@ struct Ctx {
 
 // Argument bundle handed to every AxLocal launcher.
 struct AxArgs {
-  int64_t E;
-  int N;
-  ax_geom_kind kind;
-  const void *geo;
-  const void *lam;
-  const void *X;
-  void *Y;
-  cudaStream_t stream;
+  int64_t E = 0;
+  int N = 0;
+  ax_geom_kind kind = AX_GEOM_STORED;
+  const void *geo = nullptr;
+  const void *lam = nullptr;
+  const void *X = nullptr;
+  void *Y = nullptr;
+  cudaStream_t stream = nullptr;
+  int tile = 0;      // tile variant (elements per CTA: 0 = base, 1 = twice; FP32 only)
+  int64_t grid = 0;  // CTAs to launch (0 = one per block of elements; fewer = persistent loop)
 };
 
 // Launchers (return cudaSuccess or the launch error).
@@ -108,5 +110,10 @@ cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launc
                           const AxArgs &lo, cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x,
                           const float *diag_lo, double rtol, double inner_rtol, int max_outer, int max_inner,
                           int *outer, int *inner_total, double *relres, int *converged, cudaStream_t s);
+
+// Access to a context's internals for the batch layer (ax_api.cu).
+AxArgs ax_ctx_args(const ax_ctx *c);
+const Ctx &ax_ctx_core(const ax_ctx *c);
+const double *ax_ctx_vertices(const ax_ctx *c);
 
 }  // namespace ax

@@ -1,0 +1,87 @@
+"""Batched AxLocal and batched independent PCG solves over meshes of uneven
+size and order, against the per-mesh paths of the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2504_07042_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ax():
+    from paper_2504_07042_gb300 import build
+
+    build.build()
+    from paper_2504_07042_gb300 import ax as _ax
+
+    return _ax
+
+
+def _meshes():
+    # uneven batch: orders and sizes mixed, orders repeated and out of order
+    spec = [(3, 2, 2, 3), (2, 2, 1, 5), (4, 3, 2, 1), (2, 2, 2, 7), (1, 1, 1, 3), (3, 1, 1, 9), (2, 1, 1, 5)]
+    out = []
+    for s, (ex, ey, ez, N) in enumerate(spec):
+        V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=s)
+        gid, ng = inputs.box_global_ids(ex, ey, ez, N)
+        mask = inputs.box_boundary_mask(ex, ey, ez, N)
+        out.append((V, N, gid, ng, mask))
+    return out
+
+
+def _dev(meshes):
+    return [(torch.from_numpy(V).to(DEV), N, torch.from_numpy(g).to(DEV), ng, torch.from_numpy(m).to(DEV))
+            for V, N, g, ng, m in meshes]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "f64dw"])
+def test_batch_local_equals_per_mesh(ax, prec):
+    meshes = _meshes()
+    bt = ax.AxBatch(_dev(meshes), "trilinear", prec)
+    X = torch.from_numpy(np.random.default_rng(70).uniform(-1, 1, bt.n_local)).to(DEV, bt.dtype)
+    Y = torch.full_like(X, float("nan"))
+    bt.ax_batch_local(X, Y)
+    for tuned in (False, True):
+        if tuned:
+            choice = bt.ax_batch_tune()
+            assert set(choice) == set(m[1] for m in meshes)
+            Y = torch.full_like(X, float("nan"))
+            bt.ax_batch_local(X, Y)
+        for m, (V, N, gid, ng, mask) in enumerate(meshes):
+            n = V.shape[0] * (N + 1) ** 3
+            lo = bt.local_offsets[m]
+            op = ax.Ax(torch.from_numpy(V).to(DEV), N, "trilinear", prec)
+            Ym = torch.empty(n, dtype=bt.dtype, device=DEV)
+            op.ax_local(X[lo:lo + n], Ym)
+            assert torch.equal(Ym, Y[lo:lo + n]), (m, tuned)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("fp64", 1e-9)])
+def test_batch_pcg_graph_vs_per_mesh(ax, orc, prec, tol):
+    meshes = _meshes()
+    bt = ax.AxBatch(_dev(meshes), "trilinear", prec)
+    bt.ax_batch_tune()
+    # right-hand sides: b = Q^T (w|J| f) per mesh, f = 3 pi^2 sin sin sin (oracle mass and gather)
+    bvec = np.zeros(bt.n_global)
+    for m, (V, N, gid, ng, mask) in enumerate(meshes):
+        G, _ = orc.factors(V, N)
+        XYZ = orc.nodal_coords(V, N)
+        f = 3 * np.pi ** 2 * np.sin(np.pi * XYZ[:, 0]) * np.sin(np.pi * XYZ[:, 1]) * np.sin(np.pi * XYZ[:, 2])
+        bvec[bt.global_offsets[m]:bt.global_offsets[m + 1]] = orc.gather(G[:, 6, :] * f + 0.1, gid, ng)
+    bd = torch.from_numpy(bvec).to(DEV, bt.dtype)
+    rtol = 1e-5 if prec == "fp32" else 1e-10
+    x1 = torch.zeros_like(bd)
+    it1, rr1, st1 = bt.ax_batch_pcg(bd, x1, rtol=rtol, maxit=5000, graph=1)
+    x0 = torch.zeros_like(bd)
+    it0, rr0, st0 = bt.ax_batch_pcg(bd, x0, rtol=rtol, maxit=5000, graph=0)
+    assert st1 == ax.AX_OK and st0 == ax.AX_OK
+    assert all(r <= rtol for r in rr1)
+    for m in range(bt.B):
+        a, b = bt.global_offsets[m], bt.global_offsets[m + 1]
+        d = float((x1[a:b] - x0[a:b]).abs().max()) / float(x0[a:b].abs().max())
+        assert d <= tol, (m, d)
+        assert abs(it1[m] - it0[m]) <= 2, (m, it1[m], it0[m])
