@@ -234,6 +234,70 @@ const char *ax_batch_last_error(const ax_batch *b);
 /* Release the batch (NULL accepted). */
 void ax_batch_destroy(ax_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Learned preconditioner (order N = 7 elements): a per-element MLP
+ * 536 -> 512 (GELU) -> 512 (GELU) -> 512, BF16 tensor-core GEMMs with FP32
+ * accumulation, FP32 master weights, Adam.  The paper has no counterpart;
+ * the MLP corrects the Jacobi step of a flexible CG.
+ * Element input (536 = 512 + 24): the element's local residual divided by
+ * s_e = max |r_e|, and its vertex coordinates relative to vertex 0 divided by
+ * h_e = |v1 - v0|; inputs are padded to 544 columns (zeros) in bf16.
+ * ---------------------------------------------------------------------- */
+typedef struct ax_mlp ax_mlp;
+
+/* Create with deterministic initial weights (splitmix64 + Box-Muller from seed). */
+ax_status ax_mlp_create(ax_mlp **out, uint64_t seed, void *stream);
+
+/* Number of float32 parameters; layout W1 [512][544] (columns >= 536 zero),
+ * b1 [512], W2 [512][512], b2 [512], W3 [512][512], b3 [512]. */
+int64_t ax_mlp_num_params(const ax_mlp *m);
+
+/* Copy the parameters out / in (params: host or device float32 [num_params]). */
+ax_status ax_mlp_get_params(ax_mlp *m, float *params, void *stream);
+ax_status ax_mlp_set_params(ax_mlp *m, const float *params, void *stream);
+
+/* Y (device float32 [M][512]) = MLP(X) for X device bf16 [M][544]. */
+ax_status ax_mlp_forward(ax_mlp *m, const void *X_bf16, float *Y, int64_t M, void *stream);
+
+/* Loss L = 0.5 mean (MLP(X) - T)^2 over M rows (M a positive multiple of 32)
+ * and its gradient w.r.t. every parameter (grads: host or device float32
+ * [num_params], same layout).  For gradient checks.  Synchronises. */
+ax_status ax_mlp_grad(ax_mlp *m, const void *X_bf16, const float *T, int64_t M, float *loss, float *grads,
+                      void *stream);
+
+/* Adam training (lr, beta1 0.9, beta2 0.999, eps 1e-8) on n_samples rows of
+ * X (device bf16 [n][544]) and T (device float32 [n][512]): epochs passes of
+ * shuffled mini-batches of `batch` rows (a multiple of 32).  loss_history:
+ * host float [epochs] (last batch's loss per epoch) or NULL.  Synchronises. */
+ax_status ax_mlp_train(ax_mlp *m, const void *X_bf16, const float *T, int64_t n_samples, int epochs, int batch,
+                       float lr, uint64_t seed, float *loss_history, void *stream);
+
+/* Training pairs from an iterate x_k of a solve of the context's system
+ * (gs_setup done; N = 7):  r = b - A x_k (Dirichlet-masked), e = x_star - x_k,
+ * d = Jacobi inverse diagonal.  For each listed element i (elements: device
+ * int64 [n]): F[i] (device bf16 [544]) = element input of r, and
+ * T[i] (device float32 [512]) = (h_e / s_e) (e - d r) on the element's nodes.
+ * b_global, x_star, x_k: device float64 [n_global]. */
+ax_status ax_mlp_pairs(ax_ctx *c, const double *b_global, const double *x_star, const double *x_k,
+                       const int64_t *elements, int64_t n, void *F_bf16, float *T, void *stream);
+
+/* Flexible CG (Polak-Ribiere beta) with the learned preconditioner
+ *   z = D^-1 r + omega Q^T(c) / multiplicity,   c_e = (s_e / h_e) MLP(input of r_e),
+ * on the context's Dirichlet system (float64 vectors, the context's
+ * FP64-accurate AxLocal).  Safeguards: a learned step with r . z <= 0 is
+ * replaced by the Jacobi step; if the residual has not halved for 200
+ * iterations the solve falls back to Jacobi-PCG for the rest (*fell_back = 1).
+ * Stops when ||r|| <= rtol ||b|| (AX_OK) or after maxit iterations
+ * (AX_ENOTCONV).  Synchronises. */
+ax_status pcg_solve_learned(ax_ctx *c, ax_mlp *m, const double *b_global, double *x_global, double rtol, int maxit,
+                            double omega, int *iters, double *relres, int *fell_back, void *stream);
+
+/* Message of the last failed MLP call (or of creation when m is NULL). */
+const char *ax_mlp_last_error(const ax_mlp *m);
+
+/* Release the MLP (NULL accepted). */
+void ax_mlp_destroy(ax_mlp *m);
+
 /* Algorithmic cost of one ax_local call (per element): bytes moved to and
  * from HBM by the kernel's design, the paper's effective flops
  * F_ax = 12 N1^4 + 15 N1^3 (Table 2), and the arithmetic instructions the

@@ -79,6 +79,28 @@ _lib.ax_batch_last_error.argtypes = [_vp]
 _lib.ax_batch_last_error.restype = ctypes.c_char_p
 _lib.ax_batch_destroy.argtypes = [_vp]
 _lib.ax_batch_destroy.restype = None
+_lib.ax_mlp_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_uint64, _vp]
+_lib.ax_mlp_create.restype = _int
+_lib.ax_mlp_num_params.argtypes = [_vp]
+_lib.ax_mlp_num_params.restype = _i64
+for _n in ("ax_mlp_get_params", "ax_mlp_set_params"):
+    getattr(_lib, _n).argtypes = [_vp, _vp, _vp]
+    getattr(_lib, _n).restype = _int
+_lib.ax_mlp_forward.argtypes = [_vp, _vp, _vp, _i64, _vp]
+_lib.ax_mlp_forward.restype = _int
+_lib.ax_mlp_grad.argtypes = [_vp, _vp, _vp, _i64, ctypes.POINTER(ctypes.c_float), _vp, _vp]
+_lib.ax_mlp_grad.restype = _int
+_lib.ax_mlp_train.argtypes = [_vp, _vp, _vp, _i64, _int, _int, ctypes.c_float, ctypes.c_uint64, _vp, _vp]
+_lib.ax_mlp_train.restype = _int
+_lib.ax_mlp_pairs.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]
+_lib.ax_mlp_pairs.restype = _int
+_lib.pcg_solve_learned.argtypes = [_vp, _vp, _vp, _vp, _dbl, _int, _dbl, ctypes.POINTER(_int), ctypes.POINTER(_dbl),
+                                   ctypes.POINTER(_int), _vp]
+_lib.pcg_solve_learned.restype = _int
+_lib.ax_mlp_last_error.argtypes = [_vp]
+_lib.ax_mlp_last_error.restype = ctypes.c_char_p
+_lib.ax_mlp_destroy.argtypes = [_vp]
+_lib.ax_mlp_destroy.restype = None
 _lib.ax_query.argtypes = [_vp, ctypes.POINTER(ax_info)]
 _lib.ax_query.restype = _int
 _lib.ax_last_error.argtypes = [_vp]
@@ -92,6 +114,8 @@ EXPORTS = ("ax_setup", "ax_local", "ax_local_host", "ax_local_host_static", "ax_
            "gs_setup", "gs_assemble", "gs_gather", "gs_scatter", "ax_mass", "ax_diag", "pcg_solve", "pcg_solve_mixed",
            "ax_batch_setup", "ax_batch_sizes", "ax_batch_local", "ax_batch_tune", "ax_batch_pcg",
            "ax_batch_last_error", "ax_batch_destroy",
+           "ax_mlp_create", "ax_mlp_num_params", "ax_mlp_get_params", "ax_mlp_set_params", "ax_mlp_forward",
+           "ax_mlp_grad", "ax_mlp_train", "ax_mlp_pairs", "pcg_solve_learned", "ax_mlp_last_error", "ax_mlp_destroy",
            "ax_last_error", "ax_status_string", "ax_destroy")
 
 
@@ -291,3 +315,75 @@ class AxBatch:
             self.ax_batch_destroy()
         except Exception:
             pass
+
+
+def _mcheck(st: int, m=None):
+    if st != AX_OK:
+        raise AxError(st, _lib.ax_mlp_last_error(m).decode())
+
+
+class AxMLP:
+    """Owns an ax_mlp (the learned preconditioner's network).  Names follow the C ABI."""
+
+    IN, IN_PAD, HID, OUT = 536, 544, 512, 512
+
+    def __init__(self, seed: int = 0, stream=None):
+        self.m = _vp()
+        _mcheck(_lib.ax_mlp_create(ctypes.byref(self.m), int(seed), _stream(stream)))
+        self.num_params = int(_lib.ax_mlp_num_params(self.m))
+
+    def ax_mlp_get_params(self, out=None, stream=None):
+        import numpy as np
+        out = np.empty(self.num_params, dtype=np.float32) if out is None else out
+        _mcheck(_lib.ax_mlp_get_params(self.m, _ptr(out), _stream(stream)), self.m)
+        return out
+
+    def ax_mlp_set_params(self, params, stream=None):
+        _mcheck(_lib.ax_mlp_set_params(self.m, _ptr(params), _stream(stream)), self.m)
+
+    def ax_mlp_forward(self, X_bf16, Y, stream=None):
+        _mcheck(_lib.ax_mlp_forward(self.m, _ptr(X_bf16), _ptr(Y), int(X_bf16.shape[0]), _stream(stream)), self.m)
+        return Y
+
+    def ax_mlp_grad(self, X_bf16, T, grads=None, stream=None):
+        import numpy as np
+        grads = np.empty(self.num_params, dtype=np.float32) if grads is None else grads
+        loss = ctypes.c_float(0.0)
+        _mcheck(_lib.ax_mlp_grad(self.m, _ptr(X_bf16), _ptr(T), int(X_bf16.shape[0]), ctypes.byref(loss), _ptr(grads),
+                                 _stream(stream)), self.m)
+        return loss.value, grads
+
+    def ax_mlp_train(self, X_bf16, T, epochs=4, batch=4096, lr=1e-3, seed=0, stream=None):
+        import numpy as np
+        hist = np.zeros(int(epochs), dtype=np.float32)
+        _mcheck(_lib.ax_mlp_train(self.m, _ptr(X_bf16), _ptr(T), int(X_bf16.shape[0]), int(epochs), int(batch),
+                                  float(lr), int(seed), _ptr(hist), _stream(stream)), self.m)
+        return hist
+
+    def ax_mlp_destroy(self):
+        if self.m:
+            _lib.ax_mlp_destroy(self.m)
+            self.m = _vp()
+
+    def __del__(self):
+        try:
+            self.ax_mlp_destroy()
+        except Exception:
+            pass
+
+
+def ax_mlp_pairs(op: "Ax", b_global, x_star, x_k, elements, F_bf16, T, stream=None):
+    _mcheck(_lib.ax_mlp_pairs(op.ctx, _ptr(b_global), _ptr(x_star), _ptr(x_k), _ptr(elements), int(elements.numel()),
+                              _ptr(F_bf16), _ptr(T), _stream(stream)))
+    return F_bf16, T
+
+
+def pcg_solve_learned(op: "Ax", mlp: AxMLP, b_global, x_global, rtol=1e-8, maxit=10000, omega=0.5, stream=None,
+                      check=True):
+    """Returns (iterations, relative residual, status, fell_back)."""
+    it, rr, fb = _int(0), _dbl(0.0), _int(0)
+    st = _lib.pcg_solve_learned(op.ctx, mlp.m, _ptr(b_global), _ptr(x_global), float(rtol), int(maxit), float(omega),
+                                ctypes.byref(it), ctypes.byref(rr), ctypes.byref(fb), _stream(stream))
+    if check and st not in (AX_OK, AX_ENOTCONV):
+        _mcheck(st, mlp.m)
+    return it.value, rr.value, st, fb.value

@@ -147,3 +147,19 @@ def batch_meshes(n_meshes: int = 64, seed_e: int = 4, seed_n: int = 5):
     for E, N in zip(Es, Ns):
         out.append(near_cubic_box(int(round(E))) + (int(N),))
     return out
+
+
+def smooth_rhs(XYZ: np.ndarray, seed: int, order: int = 3) -> np.ndarray:
+    """Random smooth source f(x) = sum_{a,b,c=1..order} c_abc sin(a pi x) sin(b pi y) sin(c pi z),
+    c_abc ~ N(0,1) / (a^2 + b^2 + c^2), evaluated at node coordinates XYZ [E][3][n3]
+    (rng seed `seed`; the training solves use seeds 100..299)."""
+    rng = np.random.default_rng(seed)
+    f = np.zeros(XYZ[:, 0].shape)
+    sx = [np.sin(a * np.pi * XYZ[:, 0]) for a in range(1, order + 1)]
+    sy = [np.sin(b * np.pi * XYZ[:, 1]) for b in range(1, order + 1)]
+    sz = [np.sin(c * np.pi * XYZ[:, 2]) for c in range(1, order + 1)]
+    for a in range(order):
+        for b in range(order):
+            for c in range(order):
+                f += rng.standard_normal() / ((a + 1) ** 2 + (b + 1) ** 2 + (c + 1) ** 2) * sx[a] * sy[b] * sz[c]
+    return f
