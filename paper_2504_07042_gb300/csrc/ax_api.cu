@@ -49,6 +49,10 @@ void release(ax_ctx *c) {
   cudaFree(c->c.hx);
   cudaFree(c->c.hy);
   cudaFree(c->vtx);
+  cudaFree(c->c.diag64);
+  cudaFree(c->c.diag32);
+  c->c.diag64 = nullptr;
+  c->c.diag32 = nullptr;
   ax::gs_free(c->c.gs);
   c->c.geo = c->c.lam = c->c.hx = c->c.hy = nullptr;
   c->vtx = nullptr;
@@ -84,6 +88,29 @@ bool same_device(ax_ctx *c) {
 }  // namespace
 
 namespace ax {
+cudaError_t assembled_diag(ax_ctx *c, bool f64, const void **out, cudaStream_t s) {
+  void **slot = f64 ? (void **)&c->c.diag64 : (void **)&c->c.diag32;
+  if (*slot) {
+    *out = *slot;
+    return cudaSuccess;
+  }
+  const size_t w = f64 ? 8 : 4;
+  void *dl = nullptr, *dg = nullptr;
+  cudaError_t e = cudaMalloc(&dl, w * c->c.gs.n_local + 8);
+  if (e == cudaSuccess) e = cudaMalloc(&dg, w * c->c.gs.n_global + 8);
+  if (e == cudaSuccess) e = setup_diag(c->c, c->vtx, dl, f64, s);
+  if (e == cudaSuccess) e = gs_gather_run(c->c.gs, f64, dl, dg, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dl);
+  if (e != cudaSuccess) {
+    cudaFree(dg);
+    return e;
+  }
+  *slot = dg;
+  *out = dg;
+  return cudaSuccess;
+}
+
 AxArgs ax_ctx_args(const ax_ctx *c) { return make_args(const_cast<ax_ctx *>(c), nullptr, nullptr, nullptr); }
 const Ctx &ax_ctx_core(const ax_ctx *c) { return c->c; }
 const double *ax_ctx_vertices(const ax_ctx *c) { return c->vtx; }
@@ -295,7 +322,13 @@ ax_status gs_setup(ax_ctx *c, const int64_t *global_id, int64_t n_global, const 
   const int64_t n_local = c->c.E * (int64_t)c->c.n3;
   if (n_global < 0 || (n_local > 0 && !global_id)) return fail(c, AX_EINVAL, "gs_setup: bad global ids");
   if (!same_device(c)) return fail(c, AX_EINVAL, "gs_setup: current device differs from the context's");
+  if (n_local >= ax::kMaxGsIndex || n_global >= ax::kMaxGsIndex)
+    return fail(c, AX_ERANGE, "gs_setup: more than 2^31 - 1 local or global nodes");
   ax::gs_free(c->c.gs);
+  cudaFree(c->c.diag64);
+  cudaFree(c->c.diag32);
+  c->c.diag64 = nullptr;
+  c->c.diag32 = nullptr;
   int64_t bad = 0;
   cudaError_t e = ax::gs_build(c->c.gs, global_id, n_local, n_global, dirichlet_mask, (cudaStream_t)stream, &bad);
   if (e != cudaSuccess) {
@@ -375,14 +408,10 @@ ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol
   const bool f64 = is_f64_io(c->c.prec);
   const size_t w = f64 ? 8 : 4;
   cudaStream_t s = (cudaStream_t)stream;
-  void *diag_l = nullptr, *diag_g = nullptr;
+  (void)w;
+  const void *diag_g = nullptr;
   cudaError_t e = cudaSuccess;
-  if (precond == 1) {
-    e = cudaMalloc(&diag_l, w * c->c.gs.n_local + 8);
-    if (e == cudaSuccess) e = cudaMalloc(&diag_g, w * c->c.gs.n_global);
-    if (e == cudaSuccess) e = ax::setup_diag(c->c, c->vtx, diag_l, f64, s);
-    if (e == cudaSuccess) e = ax::gs_gather_run(c->c.gs, f64, diag_l, diag_g, s);
-  }
+  if (precond == 1) e = ax::assembled_diag(c, f64, &diag_g, s);
   int conv = 0;
   cudaError_t (*launch)(const ax::AxArgs &) = nullptr;
   switch (c->c.prec) {
@@ -395,8 +424,6 @@ ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol
   if (e == cudaSuccess)
     e = ax::pcg_run(c->c.gs, f64, make_args(c, nullptr, nullptr, stream), launch, b_global, x_global, diag_g, rtol,
                     maxit, iters, relres, &conv, s);
-  cudaFree(diag_l);
-  cudaFree(diag_g);
   if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve");
   if (!conv) {
     char msg[120];
@@ -429,18 +456,14 @@ ax_status pcg_solve_mixed(ax_ctx *hi, ax_ctx *lo, const double *b_global, double
     case AX_FP32: ll = ax::launch_ax_fp32; break;
     default: return fail(lo, AX_EUNSUPPORTED, "pcg_solve_mixed: lo precision has no AxLocal kernel");
   }
-  float *diag_l = nullptr, *diag_g = nullptr;
-  cudaError_t e = cudaMalloc(&diag_l, sizeof(float) * hi->c.gs.n_local + 8);
-  if (e == cudaSuccess) e = cudaMalloc(&diag_g, sizeof(float) * hi->c.gs.n_global);
-  if (e == cudaSuccess) e = ax::setup_diag(lo->c, lo->vtx, diag_l, false, s);
-  if (e == cudaSuccess) e = ax::gs_gather_run(hi->c.gs, false, diag_l, diag_g, s);
+  // the inner solve's Jacobi diagonal: the same mesh's operator, in float32
+  const void *diag_g = nullptr;
+  cudaError_t e = ax::assembled_diag(hi, false, &diag_g, s);
   int conv = 0;
   if (e == cudaSuccess)
     e = ax::pcg_mixed_run(hi->c.gs, make_args(hi, nullptr, nullptr, stream), lh, make_args(lo, nullptr, nullptr, stream),
-                          ll, b_global, x_global, diag_g, rtol, inner_rtol, max_outer, max_inner, outer_iters,
-                          inner_iters, relres, &conv, s);
-  cudaFree(diag_l);
-  cudaFree(diag_g);
+                          ll, b_global, x_global, (const float *)diag_g, rtol, inner_rtol, max_outer, max_inner,
+                          outer_iters, inner_iters, relres, &conv, s);
   if (e != cudaSuccess) return cuda_fail(hi, e, "pcg_solve_mixed");
   if (!conv) {
     char msg[160];

@@ -62,7 +62,7 @@ struct Seg {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    seg_gather_dot(Seg sg, const int64_t *__restrict__ off, const int64_t *__restrict__ idx, const T *__restrict__ Y,
+    seg_gather_dot(Seg sg, const gidx *__restrict__ off, const gidx *__restrict__ idx, const T *__restrict__ Y,
                    T *__restrict__ w, const uint8_t *__restrict__ mask, const T *__restrict__ p,
                    double *__restrict__ part, const double *__restrict__ S) {
   const int m = sg.bmesh[blockIdx.x];
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kThreads)
   if (S[m * kS + 6] == 0.0) {
     for (int64_t g = sg.blo[blockIdx.x] + threadIdx.x; g < sg.bhi[blockIdx.x]; g += kThreads) {
       T s = T(0);
-      for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+      for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
       if (mask && mask[g]) s = T(0);
       w[g] = s;
       d += p[g] * s;
@@ -182,16 +182,16 @@ __global__ void seg_start(int B, double *S, double rtol) {
 }
 
 template <typename T>
-__global__ void scatter_u(int64_t n, const int64_t *__restrict__ gid, const T *__restrict__ u, T *__restrict__ U) {
+__global__ void scatter_u(int64_t n, const gidx *__restrict__ gid, const T *__restrict__ u, T *__restrict__ U) {
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x)
     U[m] = u[gid[m]];
 }
 template <typename T>
-__global__ void gather_u(int64_t n, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+__global__ void gather_u(int64_t n, const gidx *__restrict__ off, const gidx *__restrict__ idx,
                          const T *__restrict__ Y, T *__restrict__ y, const uint8_t *__restrict__ mask) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     T s = T(0);
-    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
     y[g] = (mask && mask[g]) ? T(0) : s;
   }
 }
@@ -335,14 +335,14 @@ ax_status ax_batch_setup(ax_batch **out, int B, const int64_t *E, const int *N, 
     b->N.push_back(N[m]);
   }
   // groups by order, meshes in batch order within a group
-  std::map<int, int> gidx;
+  std::map<int, int> group_of;
   for (int m = 0; m < B; ++m) {
-    if (!gidx.count(N[m])) {
-      gidx[N[m]] = (int)b->groups.size();
+    if (!group_of.count(N[m])) {
+      group_of[N[m]] = (int)b->groups.size();
       b->groups.emplace_back();
       b->groups.back().N = N[m];
     }
-    b->groups[gidx[N[m]]].meshes.push_back(m);
+    b->groups[group_of[N[m]]].meshes.push_back(m);
   }
   b->loc_off.assign(B, 0);
   b->glob_off.assign(B + 1, 0);
@@ -359,6 +359,10 @@ ax_status ax_batch_setup(ax_batch **out, int B, const int64_t *E, const int *N, 
     }
   }
   b->n_local = loc;
+  if (b->n_local >= kMaxGsIndex || b->n_global >= kMaxGsIndex) {
+    delete b;
+    return bfail(nullptr, AX_ERANGE, "ax_batch_setup: more than 2^31 - 1 local or global nodes");
+  }
   // group contexts over the union of their meshes' elements
   double *vtx = nullptr;
   int64_t *gid_u = nullptr;

@@ -25,7 +25,7 @@ constexpr int kRedBlocks = 1024;  // stage-1 blocks of every reduction (fixed: d
 constexpr int kRedThreads = 256;
 
 template <typename T>
-__global__ void scatter_kernel(int64_t n_local, const int64_t *__restrict__ gid, const T *__restrict__ u,
+__global__ void scatter_kernel(int64_t n_local, const gidx *__restrict__ gid, const T *__restrict__ u,
                                T *__restrict__ U) {
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n_local; m += (int64_t)gridDim.x * blockDim.x)
     U[m] = u[gid[m]];
@@ -33,23 +33,23 @@ __global__ void scatter_kernel(int64_t n_local, const int64_t *__restrict__ gid,
 
 // y[g] = sum of the local copies of g (0 on masked nodes)
 template <typename T>
-__global__ void gather_kernel(int64_t n_global, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+__global__ void gather_kernel(int64_t n_global, const gidx *__restrict__ off, const gidx *__restrict__ idx,
                               const T *__restrict__ Y, T *__restrict__ y, const uint8_t *__restrict__ mask) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
     T s = T(0);
-    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
     y[g] = (mask && mask[g]) ? T(0) : s;
   }
 }
 
 // Y <- Q Q^T Y in place
 template <typename T>
-__global__ void assemble_kernel(int64_t n_global, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+__global__ void assemble_kernel(int64_t n_global, const gidx *__restrict__ off, const gidx *__restrict__ idx,
                                 T *__restrict__ Y) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
     T s = T(0);
-    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
-    for (int64_t q = off[g]; q < off[g + 1]; ++q) Y[idx[q]] = s;
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    for (gidx q = off[g]; q < off[g + 1]; ++q) Y[idx[q]] = s;
   }
 }
 
@@ -85,21 +85,29 @@ __global__ void __launch_bounds__(kRedThreads) finish_kernel(const double *__res
   block_reduce_store(s, out);
 }
 
-// gather fused with the partial dot p . w
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
-    gather_dot_kernel(int64_t n_global, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
-                      const T *__restrict__ Y, T *__restrict__ w, const uint8_t *__restrict__ mask,
-                      const T *__restrict__ p, double *__restrict__ partial) {
-  T d = T(0);
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
-    T s = T(0);
-    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
-    if (mask && mask[g]) s = T(0);
-    w[g] = s;
-    d += p[g] * s;
+// Returns true in the block that arrives last at *cnt (after every block has
+// written its partial: a release fence before the count) and resets *cnt.
+__device__ __forceinline__ bool arrive_last(unsigned *cnt) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    if (last) *cnt = 0u;
   }
-  block_reduce_store((double)d, partial + blockIdx.x);
+  __syncthreads();
+  return last;
+}
+
+// Fixed-order sum of partial[0..nb) by one block (the last to arrive), read
+// past L1: the partials were written by other SMs in this launch.
+__device__ __forceinline__ double sum_partials(const double *partial, int nb) {
+  __shared__ double total;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) s += __ldcg(partial + q);
+  block_reduce_store(s, &total);
+  __syncthreads();
+  return total;
 }
 
 // Scalars S: [0] rz, [1] pw, [2] rr, [3] bb, [4] rz_new, [5] sigma (mixed
@@ -109,15 +117,61 @@ __global__ void __launch_bounds__(kRedThreads)
 // one thread: FP64 division is a long sequence on GB300's slow FP64 pipe.
 // Vector kernels accumulate their partial dot products in their own type T
 // (no float -> double conversions per element on the FP64 pipe).
-// Once done is set, the update kernels return at once, so iterations queued
-// after convergence leave x unchanged (the host checks every few iterations).
+// Once done is set, the kernels of an iteration return at once, so
+// iterations queued after convergence leave x unchanged (the host checks
+// every few iterations).
+//
+// One CG iteration is four launches:
+//   direction_scatter  p = z + beta p;  U = Q p              (global -> local)
+//   AxLocal            W = A_e U                             (per element)
+//   gather_dot_alpha   w = mask(Q^T W);  alpha = rz / (p.w)  (last block)
+//   update_check       x += alpha p; r -= alpha w; z = M^-1 r;
+//                      rz_new, rr; test; beta = rz_new / rz  (last block)
 constexpr int kScalars = 16;
-// x += alpha p; r -= alpha w; z = r * inv_diag (0 on masked); partials of r.z and r.r
+
+template <typename T>
+__global__ void direction_scatter_kernel(int64_t n_global, const double *__restrict__ S, const T *__restrict__ z,
+                                         T *__restrict__ p, const gidx *__restrict__ off,
+                                         const gidx *__restrict__ idx, T *__restrict__ U) {
+  if (S[6] != 0.0) return;
+  const T beta = (T)S[11];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
+    const T pg = z[g] + beta * p[g];
+    p[g] = pg;
+    for (gidx q = off[g]; q < off[g + 1]; ++q) U[idx[q]] = pg;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    update_kernel(int64_t n, const double *__restrict__ S, const T *__restrict__ p, const T *__restrict__ w,
-                  T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, const T *__restrict__ inv_diag,
-                  const uint8_t *__restrict__ mask, double *__restrict__ part_rz, double *__restrict__ part_rr) {
+    gather_dot_alpha_kernel(int64_t n_global, const gidx *__restrict__ off, const gidx *__restrict__ idx,
+                            const T *__restrict__ Y, T *__restrict__ w, const uint8_t *__restrict__ mask,
+                            const T *__restrict__ p, double *__restrict__ partial, unsigned *__restrict__ cnt,
+                            double *__restrict__ S) {
+  if (S[6] != 0.0) return;
+  T d = T(0);
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    if (mask && mask[g]) s = T(0);
+    w[g] = s;
+    d += p[g] * s;
+  }
+  block_reduce_store((double)d, partial + blockIdx.x);
+  if (!arrive_last(cnt)) return;
+  const double pw = sum_partials(partial, gridDim.x);
+  if (threadIdx.x == 0) {
+    S[1] = pw;
+    S[10] = pw != 0.0 ? S[0] / pw : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    update_check_kernel(int64_t n, double *__restrict__ S, const T *__restrict__ p, const T *__restrict__ w,
+                        T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, const T *__restrict__ inv_diag,
+                        const uint8_t *__restrict__ mask, double *__restrict__ part_rz, double *__restrict__ part_rr,
+                        unsigned *__restrict__ cnt) {
   if (S[6] != 0.0) return;
   const T alpha = (T)S[10];
   T rz = T(0), rr = T(0);
@@ -135,46 +189,23 @@ __global__ void __launch_bounds__(kRedThreads)
   block_reduce_store((double)rz, part_rz + blockIdx.x);
   __syncthreads();
   block_reduce_store((double)rr, part_rr + blockIdx.x);
-}
-
-// p = z + beta p, beta = rz_new / rz; the last block to finish moves rz_new into rz
-template <typename T>
-__global__ void direction_kernel(int64_t n, const double *__restrict__ S, const T *__restrict__ z,
-                                 T *__restrict__ p) {
-  if (S[6] != 0.0) return;
-  const T beta = (T)S[11];
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    p[g] = z[g] + beta * p[g];
-}
-
-__global__ void shift_kernel(double *S) {
-  if (S[6] == 0.0) S[0] = S[4];
-}
-
-// one block: S[1] = sum of partials (p . A p), then alpha = rz / (p . A p)
-__global__ void __launch_bounds__(kRedThreads) finish_alpha_kernel(const double *__restrict__ partial, int nb,
-                                                                   double *__restrict__ S) {
-  double s = 0.0;
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) s += partial[q];
-  block_reduce_store(s, S + 1);
-  __syncthreads();
-  if (threadIdx.x == 0) S[10] = S[1] != 0.0 ? S[0] / S[1] : 0.0;
-}
-
-// one thread: count the iteration, test convergence (||r||^2 <= tol^2) or NaN,
-// beta = rz_new / rz
-__global__ void check_kernel(double *S) {
-  if (S[6] != 0.0) return;
-  S[11] = S[0] != 0.0 ? S[4] / S[0] : 0.0;
-  const double it = S[9] + 1.0;
-  S[9] = it;
-  const double rr = S[2];
-  if (rr <= S[8]) {
-    S[6] = 1.0;
-    S[7] = it;
-  } else if (!(rr == rr)) {
-    S[6] = 1.0;
-    S[7] = -it;
+  if (!arrive_last(cnt)) return;
+  const double rz_new = sum_partials(part_rz, gridDim.x);
+  const double rr_new = sum_partials(part_rr, gridDim.x);
+  if (threadIdx.x == 0) {
+    S[4] = rz_new;
+    S[2] = rr_new;
+    S[11] = S[0] != 0.0 ? rz_new / S[0] : 0.0;
+    S[0] = rz_new;
+    const double it = S[9] + 1.0;
+    S[9] = it;
+    if (rr_new <= S[8]) {
+      S[6] = 1.0;
+      S[7] = it;
+    } else if (!(rr_new == rr_new)) {
+      S[6] = 1.0;
+      S[7] = -it;
+    }
   }
 }
 
@@ -238,7 +269,7 @@ cudaError_t gs_build(GsPlan &plan, const int64_t *gid_dev, int64_t n_local, int6
   cudaError_t e = cudaMemcpyAsync(gid.data(), gid_dev, sizeof(int64_t) * n_local, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
-  std::vector<int64_t> off((size_t)n_global + 1, 0);
+  std::vector<gidx> off((size_t)n_global + 1, 0);
   for (int64_t m = 0; m < n_local; ++m) {
     const int64_t g = gid[m];
     if (g < 0 || g >= n_global) {
@@ -249,18 +280,22 @@ cudaError_t gs_build(GsPlan &plan, const int64_t *gid_dev, int64_t n_local, int6
   }
   if (*bad_ids) return cudaSuccess;
   for (int64_t g = 0; g < n_global; ++g) off[g + 1] += off[g];
-  std::vector<int64_t> idx((size_t)n_local), fill(off.begin(), off.end() - 1);
-  for (int64_t m = 0; m < n_local; ++m) idx[fill[gid[m]]++] = m;  // increasing local order per global node
+  std::vector<gidx> idx((size_t)n_local), gid32((size_t)n_local), fill(off.begin(), off.end() - 1);
+  for (int64_t m = 0; m < n_local; ++m) {
+    gid32[m] = (gidx)gid[m];
+    idx[fill[gid[m]]++] = (gidx)m;  // increasing local order per global node
+  }
   plan.n_global = n_global;
   plan.n_local = n_local;
-  e = cudaMalloc(&plan.off, sizeof(int64_t) * (n_global + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&plan.idx, sizeof(int64_t) * (n_local > 0 ? n_local : 1));
-  if (e == cudaSuccess) e = cudaMalloc(&plan.gid, sizeof(int64_t) * (n_local > 0 ? n_local : 1));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(plan.off, off.data(), sizeof(int64_t) * (n_global + 1), cudaMemcpyHostToDevice, s);
+  const size_t nl1 = n_local > 0 ? (size_t)n_local : 1;
+  e = cudaMalloc(&plan.off, sizeof(gidx) * (n_global + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&plan.idx, sizeof(gidx) * nl1);
+  if (e == cudaSuccess) e = cudaMalloc(&plan.gid, sizeof(gidx) * nl1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(plan.off, off.data(), sizeof(gidx) * (n_global + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_local)
-    e = cudaMemcpyAsync(plan.idx, idx.data(), sizeof(int64_t) * n_local, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(plan.idx, idx.data(), sizeof(gidx) * n_local, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_local)
-    e = cudaMemcpyAsync(plan.gid, gid_dev, sizeof(int64_t) * n_local, cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyAsync(plan.gid, gid32.data(), sizeof(gidx) * n_local, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && mask_dev) {
     e = cudaMalloc(&plan.mask, n_global > 0 ? n_global : 1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(plan.mask, mask_dev, n_global, cudaMemcpyDeviceToDevice, s);
@@ -308,12 +343,21 @@ cudaError_t gs_scatter_run(const GsPlan &p, bool f64, const void *u, void *U, cu
 }
 
 // Work vectors of one CG solve (allocated once per solve, reused across the
-// inner solves of the mixed-precision driver).
+// inner solves of the mixed-precision driver), with the private stream and
+// the instantiated graph of kCheck iterations.
+constexpr int kCheck = 16;  // iterations per graph launch (between host checks)
+
 template <typename T>
 struct PcgWork {
   int64_t n = 0, nl = 0;
   T *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *Ul = nullptr, *Yl = nullptr, *inv = nullptr;
   double *S = nullptr, *part = nullptr, *hS = nullptr;
+  unsigned *cnt = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void *graph_b = nullptr;  // the (b, x) the graph was captured for
+  void *graph_x = nullptr;
   cudaError_t alloc(int64_t n_, int64_t nl_, bool jacobi) {
     n = n_;
     nl = nl_;
@@ -327,18 +371,44 @@ struct PcgWork {
     if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * gs::kScalars);
     if (e == cudaSuccess) e = cudaMemset(S, 0, sizeof(double) * gs::kScalars);
     if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 3 * gs::kRedBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(unsigned) * 2);
+    if (e == cudaSuccess) e = cudaMemset(cnt, 0, sizeof(unsigned) * 2);
     if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * gs::kScalars);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     return e;
   }
   void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ev) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
     cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(w); cudaFree(Ul); cudaFree(Yl); cudaFree(inv);
-    cudaFree(S); cudaFree(part); cudaFreeHost(hS);
+    cudaFree(S); cudaFree(part); cudaFree(cnt); cudaFreeHost(hS);
     *this = PcgWork();
   }
 };
 
+// One CG iteration (four launches) on stream s.
+template <typename T>
+static cudaError_t pcg_iteration(const GsPlan &P, const AxArgs &a, cudaError_t (*launch)(const AxArgs &),
+                                 PcgWork<T> &W, T *x, cudaStream_t s) {
+  const int64_t n = P.n_global;
+  const int RB = gs::kRedBlocks, RT = gs::kRedThreads;
+  gs::direction_scatter_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, W.S, W.z, W.p, P.off, P.idx, W.Ul);
+  cudaError_t e = launch(a);
+  if (e != cudaSuccess) return e;
+  gs::gather_dot_alpha_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask, W.p, W.part + 2 * RB, W.cnt,
+                                                   W.S);
+  gs::update_check_kernel<T><<<RB, RT, 0, s>>>(n, W.S, W.p, W.w, x, W.r, W.z, W.inv, P.mask, W.part, W.part + RB,
+                                               W.cnt + 1);
+  return cudaGetLastError();
+}
+
 // (P)CG on the assembled masked system with work W (W.inv already holds the
 // inverted diagonal when Jacobi is on).  launch() runs AxLocal on W.Ul -> W.Yl.
+// Setup runs on the caller's stream s; the iterations run as graph launches
+// of kCheck iterations on the work's private stream (ordered after s by an
+// event, and s after it on return); the host reads the scalars after each.
 template <typename T>
 static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*launch)(const AxArgs &), PcgWork<T> &W,
                             const T *b, T *x, double rtol, int maxit, int *iters, double *relres, int *converged,
@@ -374,27 +444,38 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
     gs::set_kernel<<<1, 1, 0, s>>>(S, 8, rtol * rtol * hS[3]);
     gs::set_kernel<<<1, 1, 0, s>>>(S, 6, 0.0);
     gs::set_kernel<<<1, 1, 0, s>>>(S, 9, 0.0);
-    constexpr int kCheck = 16;  // iterations queued between host checks
+    gs::set_kernel<<<1, 1, 0, s>>>(S, 11, 0.0);  // first direction: p = z
+    cudaStream_t cs = W.cs;
+    e = cudaEventRecord(W.ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, W.ev, 0);
+    a.stream = cs;
+    if (e == cudaSuccess && maxit >= kCheck && (W.graph_b != (const void *)b || W.graph_x != (void *)x)) {
+      if (W.exec) cudaGraphExecDestroy(W.exec);
+      W.exec = nullptr;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      for (int q = 0; q < kCheck && e == cudaSuccess; ++q) e = pcg_iteration<T>(P, a, launch, W, x, cs);
+      const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = ec;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&W.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e == cudaSuccess) {
+        W.graph_b = b;
+        W.graph_x = x;
+      }
+    }
     int issued = 0;
-    while (issued < maxit) {
+    while (e == cudaSuccess && issued < maxit) {
       const int block = (maxit - issued) < kCheck ? (maxit - issued) : kCheck;
-      for (int q = 0; q < block; ++q) {
-        gs::scatter_kernel<T><<<gs::grid_for(nl), 256, 0, s>>>(nl, P.gid, W.p, W.Ul);
-        e = launch(a);
-        if (e != cudaSuccess) return e;
-        gs::gather_dot_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask, W.p, part);
-        gs::finish_alpha_kernel<<<1, RT, 0, s>>>(part, RB, S);
-        gs::update_kernel<T><<<RB, RT, 0, s>>>(n, S, W.p, W.w, x, W.r, W.z, W.inv, P.mask, part, part + RB);
-        gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 4);
-        gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
-        gs::check_kernel<<<1, 1, 0, s>>>(S);
-        gs::direction_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, S, W.z, W.p);
-        gs::shift_kernel<<<1, 1, 0, s>>>(S);
+      if (block == kCheck) {
+        e = cudaGraphLaunch(W.exec, cs);
+      } else {
+        for (int q = 0; q < block && e == cudaSuccess; ++q) e = pcg_iteration<T>(P, a, launch, W, x, cs);
       }
       issued += block;
-      e = cudaMemcpyAsync(hS, S, sizeof(double) * gs::kScalars, cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) return e;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(hS, S, sizeof(double) * gs::kScalars, cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+      if (e != cudaSuccess) break;
       rnorm = std::sqrt(hS[2]);
       if (hS[6] != 0.0) {
         if (hS[7] > 0.0) {
@@ -407,6 +488,10 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
       }
       it = issued;
     }
+    const cudaError_t e2 = cudaEventRecord(W.ev, cs);
+    if (e2 == cudaSuccess) cudaStreamWaitEvent(s, W.ev, 0);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return e;
   }
   *iters = it;
   *relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;

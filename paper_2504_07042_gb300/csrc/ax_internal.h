@@ -24,11 +24,16 @@ struct GllHost {
 };
 
 // Gather-scatter plan (Eq. 1's Q): CSR from global node to local copies.
+// Gather-scatter plans index with 32-bit integers (half the index traffic of
+// every gather and scatter); gs_setup refuses larger problems with AX_ERANGE.
+using gidx = int32_t;
+constexpr int64_t kMaxGsIndex = 2147483647;
+
 struct GsPlan {
   int64_t n_global = 0, n_local = 0;
-  int64_t *off = nullptr;  // [n_global + 1]
-  int64_t *idx = nullptr;  // [n_local], local indices grouped by global node, increasing within a group
-  int64_t *gid = nullptr;  // [n_local], global id of every local node
+  gidx *off = nullptr;  // [n_global + 1]
+  gidx *idx = nullptr;  // [n_local], local indices grouped by global node, increasing within a group
+  gidx *gid = nullptr;  // [n_local], global id of every local node
   uint8_t *mask = nullptr; // [n_global] Dirichlet mask or nullptr
 };
 
@@ -49,6 +54,10 @@ struct Ctx {
   void *hx = nullptr, *hy = nullptr;
   size_t hbytes = 0;
   GsPlan gs;
+  // assembled (gathered, masked) diagonal of the operator, double and float,
+  // computed on first use after gs_setup (Jacobi preconditioning)
+  double *diag64 = nullptr;
+  float *diag32 = nullptr;
   std::string err;
 };
 
@@ -110,6 +119,10 @@ cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launc
                           const AxArgs &lo, cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x,
                           const float *diag_lo, double rtol, double inner_rtol, int max_outer, int max_inner,
                           int *outer, int *inner_total, double *relres, int *converged, cudaStream_t s);
+
+// Assembled diagonal of the context's operator on its gs plan (cached), as
+// float64 or float32 (ax_api.cu).
+cudaError_t assembled_diag(ax_ctx *c, bool f64, const void **out, cudaStream_t s);
 
 // Access to a context's internals for the batch layer (ax_api.cu).
 AxArgs ax_ctx_args(const ax_ctx *c);

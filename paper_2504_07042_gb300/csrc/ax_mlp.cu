@@ -157,7 +157,7 @@ __global__ void element_correction(int64_t n, const float *__restrict__ Y, const
 }
 
 // z[g] = dinv[g] r[g] + omega (sum of the local corrections of g) / (number of copies); 0 on masked nodes
-__global__ void precond_combine(int64_t n, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+__global__ void precond_combine(int64_t n, const gidx *__restrict__ off, const gidx *__restrict__ idx,
                                 const double *__restrict__ cl, const double *__restrict__ dinv,
                                 const double *__restrict__ r, const uint8_t *__restrict__ mask, double omega,
                                 double *__restrict__ z) {
@@ -167,7 +167,7 @@ __global__ void precond_combine(int64_t n, const int64_t *__restrict__ off, cons
       continue;
     }
     double s = 0.0;
-    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += cl[idx[q]];
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += cl[idx[q]];
     const int64_t cnt = off[g + 1] - off[g];
     z[g] = dinv[g] * r[g] + (cnt ? omega * s / (double)cnt : 0.0);
   }
@@ -179,15 +179,15 @@ __global__ void jacobi_d(int64_t n, const double *__restrict__ dinv, const doubl
     z[g] = dinv[g] * r[g];
 }
 
-__global__ void scatter_d(int64_t n, const int64_t *__restrict__ gid, const double *__restrict__ u, double *__restrict__ U) {
+__global__ void scatter_d(int64_t n, const gidx *__restrict__ gid, const double *__restrict__ u, double *__restrict__ U) {
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x)
     U[m] = u[gid[m]];
 }
-__global__ void gather_d(int64_t n, const int64_t *__restrict__ off, const int64_t *__restrict__ idx,
+__global__ void gather_d(int64_t n, const gidx *__restrict__ off, const gidx *__restrict__ idx,
                          const double *__restrict__ Y, double *__restrict__ y, const uint8_t *__restrict__ mask) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int64_t q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
     y[g] = (mask && mask[g]) ? 0.0 : s;
   }
 }
@@ -579,12 +579,12 @@ cudaError_t apply_A(const ax_ctx *c, LearnWork &W, const double *x, double *w, c
   return cudaGetLastError();
 }
 
-cudaError_t jacobi_inverse(const ax_ctx *c, LearnWork &W, cudaStream_t s) {
+cudaError_t jacobi_inverse(ax_ctx *c, LearnWork &W, cudaStream_t s) {
   const GsPlan &P = ax_ctx_core(c).gs;
-  cudaError_t e = setup_diag(ax_ctx_core(c), ax_ctx_vertices(c), W.diag_l, true, s);
+  const void *dg = nullptr;
+  cudaError_t e = assembled_diag(c, true, &dg, s);
   if (e != cudaSuccess) return e;
-  gather_d<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, P.off, P.idx, W.diag_l, W.w, P.mask);
-  inv_d<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, W.w, W.dinv, P.mask);
+  inv_d<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, (const double *)dg, W.dinv, P.mask);
   return cudaGetLastError();
 }
 
