@@ -48,6 +48,7 @@ void release(ax_ctx *c) {
   cudaFree(c->c.lam);
   cudaFree(c->c.hx);
   cudaFree(c->c.hy);
+  c->c.free_ws();
   cudaFree(c->vtx);
   cudaFree(c->c.diag64);
   cudaFree(c->c.diag32);
@@ -113,6 +114,7 @@ cudaError_t assembled_diag(ax_ctx *c, bool f64, const void **out, cudaStream_t s
 
 AxArgs ax_ctx_args(const ax_ctx *c) { return make_args(const_cast<ax_ctx *>(c), nullptr, nullptr, nullptr); }
 const Ctx &ax_ctx_core(const ax_ctx *c) { return c->c; }
+Ctx &ax_ctx_core_mut(ax_ctx *c) { return c->c; }
 const double *ax_ctx_vertices(const ax_ctx *c) { return c->vtx; }
 }  // namespace ax
 
@@ -324,6 +326,7 @@ ax_status gs_setup(ax_ctx *c, const int64_t *global_id, int64_t n_global, const 
   if (!same_device(c)) return fail(c, AX_EINVAL, "gs_setup: current device differs from the context's");
   if (n_local >= ax::kMaxGsIndex || n_global >= ax::kMaxGsIndex)
     return fail(c, AX_ERANGE, "gs_setup: more than 2^31 - 1 local or global nodes");
+  c->c.free_ws();
   ax::gs_free(c->c.gs);
   cudaFree(c->c.diag64);
   cudaFree(c->c.diag32);
@@ -422,7 +425,7 @@ ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol
   }
   if (e == cudaSuccess && !launch) e = cudaErrorNotSupported;
   if (e == cudaSuccess)
-    e = ax::pcg_run(c->c.gs, f64, make_args(c, nullptr, nullptr, stream), launch, b_global, x_global, diag_g, rtol,
+    e = ax::pcg_run(c->c, f64, make_args(c, nullptr, nullptr, stream), launch, b_global, x_global, diag_g, rtol,
                     maxit, iters, relres, &conv, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pcg_solve");
   if (!conv) {
@@ -461,7 +464,7 @@ ax_status pcg_solve_mixed(ax_ctx *hi, ax_ctx *lo, const double *b_global, double
   cudaError_t e = ax::assembled_diag(hi, false, &diag_g, s);
   int conv = 0;
   if (e == cudaSuccess)
-    e = ax::pcg_mixed_run(hi->c.gs, make_args(hi, nullptr, nullptr, stream), lh, make_args(lo, nullptr, nullptr, stream),
+    e = ax::pcg_mixed_run(hi->c, make_args(hi, nullptr, nullptr, stream), lh, make_args(lo, nullptr, nullptr, stream),
                           ll, b_global, x_global, (const float *)diag_g, rtol, inner_rtol, max_outer, max_inner,
                           outer_iters, inner_iters, relres, &conv, s);
   if (e != cudaSuccess) return cuda_fail(hi, e, "pcg_solve_mixed");

@@ -14,9 +14,11 @@
 
 #include <cmath>
 #include <cstdint>
+#include <new>
 #include <vector>
 
 #include "ax_internal.h"
+#include "reduce.cuh"
 
 namespace ax {
 namespace gs {
@@ -53,20 +55,6 @@ __global__ void assemble_kernel(int64_t n_global, const gidx *__restrict__ off, 
   }
 }
 
-// Fixed-order block reduction of v into out[blockIdx.x] (double accumulation).
-__device__ __forceinline__ void block_reduce_store(double v, double *out) {
-  __shared__ double sh[kRedThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    v = lane < kRedThreads / 32 ? sh[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) *out = v;
-  }
-}
-
 // partial[b] = sum over this block's slice of a*b
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__restrict__ a, const T *__restrict__ b,
@@ -74,7 +62,7 @@ __global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__
   double s = 0.0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     s += (double)a[g] * (double)b[g];
-  block_reduce_store(s, partial + blockIdx.x);
+  red::block_reduce_store(s, partial + blockIdx.x);
 }
 
 // final stage: out = sum(partial[0..nb)) (one block)
@@ -82,32 +70,7 @@ __global__ void __launch_bounds__(kRedThreads) finish_kernel(const double *__res
                                                              double *__restrict__ out) {
   double s = 0.0;
   for (int q = threadIdx.x; q < nb; q += blockDim.x) s += partial[q];
-  block_reduce_store(s, out);
-}
-
-// Returns true in the block that arrives last at *cnt (after every block has
-// written its partial: a release fence before the count) and resets *cnt.
-__device__ __forceinline__ bool arrive_last(unsigned *cnt) {
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
-    if (last) *cnt = 0u;
-  }
-  __syncthreads();
-  return last;
-}
-
-// Fixed-order sum of partial[0..nb) by one block (the last to arrive), read
-// past L1: the partials were written by other SMs in this launch.
-__device__ __forceinline__ double sum_partials(const double *partial, int nb) {
-  __shared__ double total;
-  double s = 0.0;
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) s += __ldcg(partial + q);
-  block_reduce_store(s, &total);
-  __syncthreads();
-  return total;
+  red::block_reduce_store(s, out);
 }
 
 // Scalars S: [0] rz, [1] pw, [2] rr, [3] bb, [4] rz_new, [5] sigma (mixed
@@ -157,9 +120,9 @@ __global__ void __launch_bounds__(kRedThreads)
     w[g] = s;
     d += p[g] * s;
   }
-  block_reduce_store((double)d, partial + blockIdx.x);
-  if (!arrive_last(cnt)) return;
-  const double pw = sum_partials(partial, gridDim.x);
+  red::block_reduce_store((double)d, partial + blockIdx.x);
+  if (!red::arrive_last(cnt)) return;
+  const double pw = red::sum_partials(partial, gridDim.x);
   if (threadIdx.x == 0) {
     S[1] = pw;
     S[10] = pw != 0.0 ? S[0] / pw : 0.0;
@@ -186,12 +149,12 @@ __global__ void __launch_bounds__(kRedThreads)
     rz += rg * zg;
     rr += rg * rg;
   }
-  block_reduce_store((double)rz, part_rz + blockIdx.x);
+  red::block_reduce_store((double)rz, part_rz + blockIdx.x);
   __syncthreads();
-  block_reduce_store((double)rr, part_rr + blockIdx.x);
-  if (!arrive_last(cnt)) return;
-  const double rz_new = sum_partials(part_rz, gridDim.x);
-  const double rr_new = sum_partials(part_rr, gridDim.x);
+  red::block_reduce_store((double)rr, part_rr + blockIdx.x);
+  if (!red::arrive_last(cnt)) return;
+  const double rz_new = red::sum_partials(part_rz, gridDim.x);
+  const double rr_new = red::sum_partials(part_rr, gridDim.x);
   if (threadIdx.x == 0) {
     S[4] = rz_new;
     S[2] = rr_new;
@@ -230,11 +193,11 @@ __global__ void __launch_bounds__(kRedThreads)
     rr += rg * rg;
     bb += bg * bg;
   }
-  block_reduce_store((double)rz, part_rz + blockIdx.x);
+  red::block_reduce_store((double)rz, part_rz + blockIdx.x);
   __syncthreads();
-  block_reduce_store((double)rr, part_rr + blockIdx.x);
+  red::block_reduce_store((double)rr, part_rr + blockIdx.x);
   __syncthreads();
-  block_reduce_store((double)bb, part_bb + blockIdx.x);
+  red::block_reduce_store((double)bb, part_bb + blockIdx.x);
 }
 
 template <typename T>
@@ -356,8 +319,12 @@ struct PcgWork {
   cudaStream_t cs = nullptr;
   cudaEvent_t ev = nullptr;
   cudaGraphExec_t exec = nullptr;
-  const void *graph_b = nullptr;  // the (b, x) the graph was captured for
+  const void *graph_b = nullptr;  // the (b, x, preconditioner, operator) the graph was captured for
   void *graph_x = nullptr;
+  bool graph_jac = false;
+  const void *graph_op = nullptr;
+  bool jac = false;  // Jacobi on: inv holds the inverted diagonal
+  T *inv_or_null() const { return jac ? inv : nullptr; }
   cudaError_t alloc(int64_t n_, int64_t nl_, bool jacobi) {
     n = n_;
     nl = nl_;
@@ -367,7 +334,8 @@ struct PcgWork {
     if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(T) * n);
     if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(T) * nl);
     if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(T) * nl);
-    if (e == cudaSuccess && jacobi) e = cudaMalloc(&inv, sizeof(T) * n);
+    (void)jacobi;
+    if (e == cudaSuccess) e = cudaMalloc(&inv, sizeof(T) * n);
     if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * gs::kScalars);
     if (e == cudaSuccess) e = cudaMemset(S, 0, sizeof(double) * gs::kScalars);
     if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 3 * gs::kRedBlocks);
@@ -399,7 +367,7 @@ static cudaError_t pcg_iteration(const GsPlan &P, const AxArgs &a, cudaError_t (
   if (e != cudaSuccess) return e;
   gs::gather_dot_alpha_kernel<T><<<RB, RT, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask, W.p, W.part + 2 * RB, W.cnt,
                                                    W.S);
-  gs::update_check_kernel<T><<<RB, RT, 0, s>>>(n, W.S, W.p, W.w, x, W.r, W.z, W.inv, P.mask, W.part, W.part + RB,
+  gs::update_check_kernel<T><<<RB, RT, 0, s>>>(n, W.S, W.p, W.w, x, W.r, W.z, W.inv_or_null(), P.mask, W.part, W.part + RB,
                                                W.cnt + 1);
   return cudaGetLastError();
 }
@@ -428,7 +396,8 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
   cudaError_t e = launch(a);
   if (e != cudaSuccess) return e;
   gs::gather_kernel<T><<<gs::grid_for(n), 256, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask);
-  gs::init_kernel<T><<<RB, RT, 0, s>>>(n, b, W.w, W.r, W.z, W.p, W.inv, P.mask, part, part + RB, part + 2 * RB);
+  gs::init_kernel<T><<<RB, RT, 0, s>>>(n, b, W.w, W.r, W.z, W.p, W.inv_or_null(), P.mask, part, part + RB,
+                                       part + 2 * RB);
   gs::finish_kernel<<<1, RT, 0, s>>>(part, RB, S + 0);
   gs::finish_kernel<<<1, RT, 0, s>>>(part + RB, RB, S + 2);
   gs::finish_kernel<<<1, RT, 0, s>>>(part + 2 * RB, RB, S + 3);
@@ -449,7 +418,9 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
     e = cudaEventRecord(W.ev, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, W.ev, 0);
     a.stream = cs;
-    if (e == cudaSuccess && maxit >= kCheck && (W.graph_b != (const void *)b || W.graph_x != (void *)x)) {
+    if (e == cudaSuccess && maxit >= kCheck &&
+        (!W.exec || W.graph_b != (const void *)b || W.graph_x != (void *)x || W.graph_jac != W.jac ||
+         W.graph_op != base.geo)) {
       if (W.exec) cudaGraphExecDestroy(W.exec);
       W.exec = nullptr;
       cudaGraph_t graph = nullptr;
@@ -462,6 +433,8 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
       if (e == cudaSuccess) {
         W.graph_b = b;
         W.graph_x = x;
+        W.graph_jac = W.jac;
+        W.graph_op = base.geo;
       }
     }
     int issued = 0;
@@ -501,26 +474,57 @@ static cudaError_t pcg_core(const GsPlan &P, const AxArgs &base, cudaError_t (*l
 }
 
 template <typename T>
-static cudaError_t pcg_t(const GsPlan &P, const AxArgs &base, cudaError_t (*launch)(const AxArgs &), const T *b, T *x,
-                         const T *diag_global, double rtol, int maxit, int *iters, double *relres, int *converged,
-                         cudaStream_t s) {
-  PcgWork<T> W;
-  cudaError_t e = W.alloc(P.n_global, P.n_local, diag_global != nullptr);
-  if (e == cudaSuccess && diag_global)
-    gs::invert_kernel<T><<<gs::grid_for(P.n_global), 256, 0, s>>>(P.n_global, diag_global, W.inv, P.mask);
-  if (e == cudaSuccess) e = pcg_core<T>(P, base, launch, W, b, x, rtol, maxit, iters, relres, converged, s);
-  W.release();
-  return e;
+static void delete_work(void *p) {
+  PcgWork<T> *W = static_cast<PcgWork<T> *>(p);
+  W->release();
+  delete W;
 }
 
-cudaError_t pcg_run(const GsPlan &P, bool f64, const AxArgs &base, cudaError_t (*launch)(const AxArgs &),
-                    const void *b, void *x, const void *diag_global, double rtol, int maxit, int *iters,
-                    double *relres, int *converged, cudaStream_t s) {
+// The context's cached work of type T (allocated on first use).
+template <typename T>
+static cudaError_t cached_work(Ctx &ctx, int slot, PcgWork<T> **out) {
+  PcgWork<T> *W = static_cast<PcgWork<T> *>(ctx.ws[slot]);
+  if (W && (W->n != ctx.gs.n_global || W->nl != ctx.gs.n_local)) {
+    ctx.ws_del[slot](W);
+    ctx.ws[slot] = nullptr;
+    W = nullptr;
+  }
+  if (!W) {
+    W = new (std::nothrow) PcgWork<T>;
+    if (!W) return cudaErrorMemoryAllocation;
+    cudaError_t e = W->alloc(ctx.gs.n_global, ctx.gs.n_local, true);
+    if (e != cudaSuccess) {
+      delete_work<T>(W);
+      return e;
+    }
+    ctx.ws[slot] = W;
+    ctx.ws_del[slot] = delete_work<T>;
+  }
+  *out = W;
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t pcg_t(Ctx &ctx, int slot, const AxArgs &base, cudaError_t (*launch)(const AxArgs &), const T *b,
+                         T *x, const T *diag_global, double rtol, int maxit, int *iters, double *relres,
+                         int *converged, cudaStream_t s) {
+  const GsPlan &P = ctx.gs;
+  PcgWork<T> *W = nullptr;
+  cudaError_t e = cached_work<T>(ctx, slot, &W);
+  if (e != cudaSuccess) return e;
+  W->jac = diag_global != nullptr;
+  if (W->jac) gs::invert_kernel<T><<<gs::grid_for(P.n_global), 256, 0, s>>>(P.n_global, diag_global, W->inv, P.mask);
+  return pcg_core<T>(P, base, launch, *W, b, x, rtol, maxit, iters, relres, converged, s);
+}
+
+cudaError_t pcg_run(Ctx &ctx, bool f64, const AxArgs &base, cudaError_t (*launch)(const AxArgs &), const void *b,
+                    void *x, const void *diag_global, double rtol, int maxit, int *iters, double *relres,
+                    int *converged, cudaStream_t s) {
   if (f64)
-    return pcg_t<double>(P, base, launch, (const double *)b, (double *)x, (const double *)diag_global, rtol, maxit,
-                         iters, relres, converged, s);
-  return pcg_t<float>(P, base, launch, (const float *)b, (float *)x, (const float *)diag_global, rtol, maxit, iters,
-                      relres, converged, s);
+    return pcg_t<double>(ctx, Ctx::kWsCg64, base, launch, (const double *)b, (double *)x, (const double *)diag_global,
+                         rtol, maxit, iters, relres, converged, s);
+  return pcg_t<float>(ctx, Ctx::kWsCg32, base, launch, (const float *)b, (float *)x, (const float *)diag_global, rtol,
+                      maxit, iters, relres, converged, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(kRedThreads) norms_kernel(int64_t n, const dou
     s += r[g] * r[g];
     m = fmax(m, fabs(r[g]));
   }
-  block_reduce_store(s, part2 + blockIdx.x);
+  red::block_reduce_store(s, part2 + blockIdx.x);
   __syncthreads();
   // max: fixed-order warp/block max
   __shared__ double sh[kRedThreads / 32];
@@ -586,37 +590,77 @@ __global__ void correct_kernel(int64_t n, const float *__restrict__ d32, const d
 }
 }  // namespace gs
 
-cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launch_hi)(const AxArgs &),
-                          const AxArgs &lo, cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x,
-                          const float *diag_lo, double rtol, double inner_rtol, int max_outer, int max_inner,
-                          int *outer, int *inner_total, double *relres, int *converged, cudaStream_t s) {
-  const int64_t n = P.n_global, nl = P.n_local;
-  const int RB = gs::kRedBlocks, RT = gs::kRedThreads;
+// Work of the mixed-precision driver: the inner float32 CG work plus the
+// outer float64 vectors (kept in the high-precision context between calls).
+struct MixedWork {
   PcgWork<float> W;
   double *r = nullptr, *w = nullptr, *Ul = nullptr, *Yl = nullptr, *S = nullptr, *part = nullptr, *hS = nullptr;
   float *r32 = nullptr, *d32 = nullptr;
+  cudaError_t alloc(int64_t n, int64_t nl) {
+    cudaError_t e = W.alloc(n, nl, true);
+    if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(double) * nl);
+    if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(double) * nl);
+    if (e == cudaSuccess) e = cudaMalloc(&r32, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d32, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * gs::kScalars);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 2 * gs::kRedBlocks);
+    if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * gs::kScalars);
+    return e;
+  }
+  void release() {
+    W.release();
+    cudaFree(r); cudaFree(w); cudaFree(Ul); cudaFree(Yl); cudaFree(r32); cudaFree(d32);
+    cudaFree(S); cudaFree(part); cudaFreeHost(hS);
+  }
+};
+static void delete_mixed(void *p) {
+  MixedWork *M = static_cast<MixedWork *>(p);
+  M->release();
+  delete M;
+}
+
+cudaError_t pcg_mixed_run(Ctx &ctx, const AxArgs &hi, cudaError_t (*launch_hi)(const AxArgs &), const AxArgs &lo,
+                          cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x, const float *diag_lo,
+                          double rtol, double inner_rtol, int max_outer, int max_inner, int *outer, int *inner_total,
+                          double *relres, int *converged, cudaStream_t s) {
+  const GsPlan &P = ctx.gs;
+  const int64_t n = P.n_global, nl = P.n_local;
+  const int RB = gs::kRedBlocks, RT = gs::kRedThreads;
   *outer = 0;
   *inner_total = 0;
   *relres = 0.0;
   *converged = 0;
-  cudaError_t e = W.alloc(n, nl, diag_lo != nullptr);
-  if (e == cudaSuccess) e = cudaMalloc(&r, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(double) * nl);
-  if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(double) * nl);
-  if (e == cudaSuccess) e = cudaMalloc(&r32, sizeof(float) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&d32, sizeof(float) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * gs::kScalars);
-  if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 2 * RB);
-  if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * gs::kScalars);
-  if (e == cudaSuccess && diag_lo)
-    gs::invert_kernel<float><<<gs::grid_for(n), 256, 0, s>>>(n, diag_lo, W.inv, P.mask);
+  MixedWork *MW = static_cast<MixedWork *>(ctx.ws[Ctx::kWsMixed]);
+  cudaError_t e = cudaSuccess;
+  if (MW && (MW->W.n != n || MW->W.nl != nl)) {
+    delete_mixed(MW);
+    ctx.ws[Ctx::kWsMixed] = nullptr;
+    MW = nullptr;
+  }
+  if (!MW) {
+    MW = new (std::nothrow) MixedWork;
+    if (!MW) return cudaErrorMemoryAllocation;
+    e = MW->alloc(n, nl);
+    if (e != cudaSuccess) {
+      delete_mixed(MW);
+      return e;
+    }
+    ctx.ws[Ctx::kWsMixed] = MW;
+    ctx.ws_del[Ctx::kWsMixed] = delete_mixed;
+  }
+  PcgWork<float> &W = MW->W;
+  double *r = MW->r, *w = MW->w, *Ul = MW->Ul, *Yl = MW->Yl, *S = MW->S, *part = MW->part, *hS = MW->hS;
+  float *r32 = MW->r32, *d32 = MW->d32;
+  W.jac = diag_lo != nullptr;
+  if (W.jac) gs::invert_kernel<float><<<gs::grid_for(n), 256, 0, s>>>(n, diag_lo, W.inv, P.mask);
   AxArgs ah = hi;
   ah.X = Ul;
   ah.Y = Yl;
   ah.stream = s;
   double bnorm = 0.0;
-  if (e == cudaSuccess) {
+  {
     // ||b|| over the unmasked nodes: r = b - 0 (masked)
     gs::mask_zero_kernel<double><<<gs::grid_for(n), 256, 0, s>>>(n, x, P.mask);
     e = cudaMemsetAsync(w, 0, sizeof(double) * n, s);
@@ -659,9 +703,6 @@ cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launc
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  W.release();
-  cudaFree(r); cudaFree(w); cudaFree(Ul); cudaFree(Yl); cudaFree(r32); cudaFree(d32);
-  cudaFree(S); cudaFree(part); cudaFreeHost(hS);
   return e;
 }
 

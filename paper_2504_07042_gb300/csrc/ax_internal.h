@@ -58,6 +58,18 @@ struct Ctx {
   // computed on first use after gs_setup (Jacobi preconditioning)
   double *diag64 = nullptr;
   float *diag32 = nullptr;
+  // solver workspaces kept between calls (work vectors, streams, captured
+  // graphs), each with its deleter; freed by gs_setup and ax_destroy
+  enum { kWsCg64 = 0, kWsCg32 = 1, kWsMixed = 2, kWsLearn = 3, kNumWs = 4 };
+  void *ws[kNumWs] = {nullptr, nullptr, nullptr, nullptr};
+  void (*ws_del[kNumWs])(void *) = {nullptr, nullptr, nullptr, nullptr};
+  void free_ws() {
+    for (int q = 0; q < kNumWs; ++q) {
+      if (ws[q] && ws_del[q]) ws_del[q](ws[q]);
+      ws[q] = nullptr;
+      ws_del[q] = nullptr;
+    }
+  }
   std::string err;
 };
 
@@ -112,13 +124,14 @@ void gs_free(GsPlan &plan);
 cudaError_t gs_assemble_run(const GsPlan &p, bool f64, void *Y, cudaStream_t s);
 cudaError_t gs_gather_run(const GsPlan &p, bool f64, const void *Y, void *y, cudaStream_t s);
 cudaError_t gs_scatter_run(const GsPlan &p, bool f64, const void *u, void *U, cudaStream_t s);
-cudaError_t pcg_run(const GsPlan &P, bool f64, const AxArgs &base, cudaError_t (*launch)(const AxArgs &),
-                    const void *b, void *x, const void *diag_global, double rtol, int maxit, int *iters,
-                    double *relres, int *converged, cudaStream_t s);
-cudaError_t pcg_mixed_run(const GsPlan &P, const AxArgs &hi, cudaError_t (*launch_hi)(const AxArgs &),
-                          const AxArgs &lo, cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x,
-                          const float *diag_lo, double rtol, double inner_rtol, int max_outer, int max_inner,
-                          int *outer, int *inner_total, double *relres, int *converged, cudaStream_t s);
+// (P)CG on ctx's gs plan; the work buffers live in ctx.ws (kept between calls)
+cudaError_t pcg_run(Ctx &ctx, bool f64, const AxArgs &base, cudaError_t (*launch)(const AxArgs &), const void *b,
+                    void *x, const void *diag_global, double rtol, int maxit, int *iters, double *relres,
+                    int *converged, cudaStream_t s);
+cudaError_t pcg_mixed_run(Ctx &ctx, const AxArgs &hi, cudaError_t (*launch_hi)(const AxArgs &), const AxArgs &lo,
+                          cudaError_t (*launch_lo)(const AxArgs &), const double *b, double *x, const float *diag_lo,
+                          double rtol, double inner_rtol, int max_outer, int max_inner, int *outer, int *inner_total,
+                          double *relres, int *converged, cudaStream_t s);
 
 // Assembled diagonal of the context's operator on its gs plan (cached), as
 // float64 or float32 (ax_api.cu).
@@ -127,6 +140,7 @@ cudaError_t assembled_diag(ax_ctx *c, bool f64, const void **out, cudaStream_t s
 // Access to a context's internals for the batch layer (ax_api.cu).
 AxArgs ax_ctx_args(const ax_ctx *c);
 const Ctx &ax_ctx_core(const ax_ctx *c);
+Ctx &ax_ctx_core_mut(ax_ctx *c);
 const double *ax_ctx_vertices(const ax_ctx *c);
 
 }  // namespace ax

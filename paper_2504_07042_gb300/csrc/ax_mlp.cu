@@ -1,5 +1,5 @@
 // Learned per-element preconditioner: a small MLP, trained and run on the GPU
-// with the BF16 tensor-core GEMM of gemm_bf16.cuh (FP32 accumulation, FP32
+// with the tcgen05 BF16 GEMM of gemm_tc.cuh (FP32 accumulation in TMEM, FP32
 // master weights, Adam), and the flexible PCG that uses it.
 //
 // Network: in_dim -> hidden (GELU) -> hidden (GELU) -> out_dim (linear).
@@ -21,7 +21,8 @@
 #include <vector>
 
 #include "ax_internal.h"
-#include "gemm_bf16.cuh"
+#include "gemm_tc.cuh"
+#include "reduce.cuh"
 
 namespace ax {
 namespace mlp {
@@ -105,78 +106,58 @@ __global__ void gather_rows(int64_t n, const int64_t *__restrict__ idx, const __
   for (int c = threadIdx.x; c < ldt; c += blockDim.x) Tb[r * ldt + c] = T[src * ldt + c];
 }
 
-// Element inputs: one CTA (256 threads) per listed element (all elements when
-// list is null).  rl: local residual [E][512] float64; V: vertices [E][24].
-// Writes F[i][0..543] (bf16) and scale[i] = s_e / h_e.
-__global__ void __launch_bounds__(256)
+// Element inputs: one warp per listed element (all elements when list is
+// null), 8 warps per CTA.  rl: local residual [E][512] float64; V: vertices
+// [E][24].  Writes F[i][0..543] (bf16) and scale[i] = s_e / h_e (float).  The
+// residual is converted to float once and everything after runs on the FP32
+// pipe (a float64 division per value would bind the kernel to GB300's FP64
+// rate).
+constexpr int kInputWarps = 8;
+__global__ void __launch_bounds__(32 * kInputWarps)
     element_inputs(int64_t n, const int64_t *__restrict__ list, const double *__restrict__ rl,
-                   const double *__restrict__ V, __nv_bfloat16 *__restrict__ F, double *__restrict__ scale) {
-  const int64_t i = blockIdx.x;
-  if (i >= n) return;
+                   const double *__restrict__ V, __nv_bfloat16 *__restrict__ F, float *__restrict__ scale,
+                   const double *__restrict__ skip) {
+  const int64_t i = (int64_t)blockIdx.x * kInputWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n || (skip && *skip != 0.0)) return;
   const int64_t e = list ? list[i] : i;
-  const double *r = rl + e * kOut;
-  __shared__ double red[256];
-  double mx = 0.0;
-  for (int l = threadIdx.x; l < kOut; l += 256) mx = fmax(mx, fabs(r[l]));
-  red[threadIdx.x] = mx;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
+  const double2 *r2 = reinterpret_cast<const double2 *>(rl + e * kOut);
+  float v[16];
+  float mx = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {  // pairs (2 lane + 64 k, +1): coalesced 16-byte loads
+    const double2 d = r2[lane + 32 * k];
+    v[2 * k] = (float)d.x;
+    v[2 * k + 1] = (float)d.y;
+    mx = fmaxf(mx, fmaxf(fabsf(v[2 * k]), fabsf(v[2 * k + 1])));
   }
-  const double se = red[0] > 0.0 ? red[0] : 1.0;
-  const double *v = V + e * 24;
-  const double dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
-  const double he = sqrt(dx * dx + dy * dy + dz * dz);
-  __nv_bfloat16 *f = F + i * kInPad;
-  for (int l = threadIdx.x; l < kOut; l += 256) f[l] = __float2bfloat16_rn((float)(r[l] / se));
-  for (int q = threadIdx.x; q < kInPad - kOut; q += 256)
-    f[kOut + q] = __float2bfloat16_rn(q < 24 ? (float)((v[q] - v[q % 3]) / he) : 0.0f);
-  if (threadIdx.x == 0 && scale) scale[i] = se / he;
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float se = mx > 0.0f ? mx : 1.0f, inv_se = 1.0f / se;
+  const double *vt = V + e * 24;
+  const float dx = (float)(vt[3] - vt[0]), dy = (float)(vt[4] - vt[1]), dz = (float)(vt[5] - vt[2]);
+  const float he = sqrtf(dx * dx + dy * dy + dz * dz), inv_he = 1.0f / he;
+  __nv_bfloat162 *f2 = reinterpret_cast<__nv_bfloat162 *>(F + i * kInPad);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f2[lane + 32 * k] = __floats2bfloat162_rn(v[2 * k] * inv_se, v[2 * k + 1] * inv_se);
+  // 32 trailing inputs: 24 relative vertex coordinates / h_e, then zero padding
+  F[i * kInPad + kOut + lane] = __float2bfloat16_rn(lane < 24 ? (float)(vt[lane] - vt[lane % 3]) * inv_he : 0.0f);
+  if (lane == 0 && scale) scale[i] = se * inv_he;
 }
+inline unsigned input_blocks(int64_t n) { return (unsigned)((n + kInputWarps - 1) / kInputWarps); }
 
-// T[i][l] = (e_l - d_l r_l) / scale[i]   (local copies; el, dl, rl [E][512])
-__global__ void element_targets(int64_t n, const int64_t *__restrict__ list, const double *__restrict__ el,
-                                const double *__restrict__ dl, const double *__restrict__ rl,
-                                const double *__restrict__ scale, float *__restrict__ T) {
+// T[i][l] = (e_g - dinv_g r_l) / scale[i] with g = gid[e][l] (e, dinv global; rl local [E][512])
+__global__ void element_targets(int64_t n, const int64_t *__restrict__ list, const gidx *__restrict__ gid,
+                                const double *__restrict__ eg, const double *__restrict__ dinv,
+                                const double *__restrict__ rl, const float *__restrict__ scale, float *__restrict__ T) {
   const int64_t i = blockIdx.x;
   if (i >= n) return;
   const int64_t e = list ? list[i] : i;
-  const double inv = 1.0 / scale[i];
+  const double inv = 1.0 / (double)scale[i];
   for (int l = threadIdx.x; l < kOut; l += blockDim.x) {
     const int64_t q = e * kOut + l;
-    T[i * kOut + l] = (float)((el[q] - dl[q] * rl[q]) * inv);
+    const gidx g = gid[q];
+    T[i * kOut + l] = (float)((eg[g] - dinv[g] * rl[q]) * inv);
   }
-}
-
-// correction of every element: cl[e][l] = Y[e][l] * scale[e]
-__global__ void element_correction(int64_t n, const float *__restrict__ Y, const double *__restrict__ scale,
-                                   double *__restrict__ cl) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * kOut; q += (int64_t)gridDim.x * blockDim.x)
-    cl[q] = (double)Y[q] * scale[q / kOut];
-}
-
-// z[g] = dinv[g] r[g] + omega (sum of the local corrections of g) / (number of copies); 0 on masked nodes
-__global__ void precond_combine(int64_t n, const gidx *__restrict__ off, const gidx *__restrict__ idx,
-                                const double *__restrict__ cl, const double *__restrict__ dinv,
-                                const double *__restrict__ r, const uint8_t *__restrict__ mask, double omega,
-                                double *__restrict__ z) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    if (mask && mask[g]) {
-      z[g] = 0.0;
-      continue;
-    }
-    double s = 0.0;
-    for (gidx q = off[g]; q < off[g + 1]; ++q) s += cl[idx[q]];
-    const int64_t cnt = off[g + 1] - off[g];
-    z[g] = dinv[g] * r[g] + (cnt ? omega * s / (double)cnt : 0.0);
-  }
-}
-
-// z = dinv r (the Jacobi step, also the fallback)
-__global__ void jacobi_d(int64_t n, const double *__restrict__ dinv, const double *__restrict__ r, double *__restrict__ z) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    z[g] = dinv[g] * r[g];
 }
 
 __global__ void scatter_d(int64_t n, const gidx *__restrict__ gid, const double *__restrict__ u, double *__restrict__ U) {
@@ -201,30 +182,221 @@ __global__ void inv_d(int64_t n, const double *__restrict__ d, double *__restric
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     inv[g] = (mask && mask[g]) ? 0.0 : 1.0 / d[g];
 }
-// fixed-order dot: partial per block, then host sum of the 1024 partials
-__global__ void __launch_bounds__(256) dot_d(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
-                                             double *__restrict__ part) {
-  __shared__ double sh[256];
-  double s = 0.0;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    s += a[g] * b[g];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
+// ---------------------------------------------------------------------------
+// learned flexible PCG: every scalar stays on the device; one iteration is
+//   lp_direction   p = z + beta p (z = D^-1 r when the Jacobi step was chosen); U = Q p
+//   AxLocal        W = A_e U
+//   lp_gather      w = mask(Q^T W); alpha = rz / (p . w)
+//   lp_update      x += alpha p; r -= alpha w; U = Q r; test ||r||; patience
+//   element_inputs, 3 GEMMs (the MLP on every element's residual)
+//   lp_precond     z = D^-1 r + omega Q^T(c)/multiplicity; safeguard; beta
+// with the flexible (Polak-Ribiere) beta = z_new . (r_new - r_old) / rz_old
+// = -alpha (z_new . w) / rz_old.
+// ---------------------------------------------------------------------------
+enum LpScalar {
+  kRz = 0, kPw = 1, kRr = 2, kBb = 3, kUseJac = 5, kDone = 6, kConvIt = 7, kTol2 = 8, kIter = 9, kAlpha = 10,
+  kBeta = 11, kBestRr = 12, kBestIt = 13, kLearnOff = 14, kMlpSkip = 15, kPatience = 16, kLpScalars = 24
+};
+constexpr int kLpBlocks = 1024;
+
+__global__ void __launch_bounds__(red::kThreads)
+    lp_init(int64_t n, const double *__restrict__ b, const double *__restrict__ w, double *__restrict__ bm,
+            double *__restrict__ r, double *__restrict__ p, const uint8_t *__restrict__ mask, double rtol,
+            double patience, double *__restrict__ part, unsigned *__restrict__ cnt, double *__restrict__ S) {
+  double bb = 0.0, rr = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const bool m = mask && mask[g];
+    const double bg = m ? 0.0 : b[g];
+    const double rg = m ? 0.0 : bg - w[g];
+    bm[g] = bg;
+    r[g] = rg;
+    p[g] = 0.0;
+    bb += bg * bg;
+    rr += rg * rg;
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  red::block_reduce_store(bb, part + blockIdx.x);
+  __syncthreads();
+  red::block_reduce_store(rr, part + kLpBlocks + blockIdx.x);
+  if (!red::arrive_last(cnt)) return;
+  const double bbt = red::sum_partials(part, gridDim.x);
+  const double rrt = red::sum_partials(part + kLpBlocks, gridDim.x);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kLpScalars; ++q) S[q] = 0.0;
+    S[kBb] = bbt;
+    S[kRr] = rrt;
+    S[kBestRr] = rrt;
+    S[kTol2] = rtol * rtol * bbt;
+    S[kPatience] = patience;
+  }
 }
-// y += a x
-__global__ void axpy_d(int64_t n, double a, const double *__restrict__ x, double *__restrict__ y) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    y[g] += a * x[g];
+
+// U = Q r (the local copies of the residual, the network's input)
+__global__ void lp_scatter(int64_t n, const double *__restrict__ r, const gidx *__restrict__ off,
+                           const gidx *__restrict__ idx, double *__restrict__ U) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double rg = r[g];
+    for (gidx q = off[g]; q < off[g + 1]; ++q) U[idx[q]] = rg;
+  }
 }
-// p = z + beta p
-__global__ void xpby_d(int64_t n, const double *__restrict__ z, double beta, double *__restrict__ p) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    p[g] = z[g] + beta * p[g];
+
+__global__ void lp_direction(int64_t n, const double *__restrict__ S, const double *__restrict__ z,
+                             const double *__restrict__ r, const double *__restrict__ dinv, double *__restrict__ p,
+                             const gidx *__restrict__ off, const gidx *__restrict__ idx, double *__restrict__ U) {
+  if (S[kDone] != 0.0) return;
+  const double beta = S[kBeta];
+  const bool jac = S[kUseJac] != 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double zg = jac ? dinv[g] * r[g] : z[g];
+    const double pg = zg + beta * p[g];
+    p[g] = pg;
+    for (gidx q = off[g]; q < off[g + 1]; ++q) U[idx[q]] = pg;
+  }
+}
+
+__global__ void __launch_bounds__(red::kThreads)
+    lp_gather(int64_t n, const gidx *__restrict__ off, const gidx *__restrict__ idx, const double *__restrict__ Y,
+              double *__restrict__ w, const uint8_t *__restrict__ mask, const double *__restrict__ p,
+              double *__restrict__ part, unsigned *__restrict__ cnt, double *__restrict__ S) {
+  if (S[kDone] != 0.0) return;
+  double d = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    if (mask && mask[g]) s = 0.0;
+    w[g] = s;
+    d += p[g] * s;
+  }
+  red::block_reduce_store(d, part + blockIdx.x);
+  if (!red::arrive_last(cnt)) return;
+  const double pw = red::sum_partials(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    S[kPw] = pw;
+    S[kAlpha] = pw != 0.0 ? S[kRz] / pw : 0.0;
+  }
+}
+
+// After the update the residual either converged (done), or the patience
+// test runs: ||r|| must halve (rr drop to a quarter) within `patience`
+// iterations of the last halving, else the learned step is switched off for
+// good (the solve continues as Jacobi-PCG).
+__global__ void __launch_bounds__(red::kThreads)
+    lp_update(int64_t n, double *__restrict__ S, const double *__restrict__ p, const double *__restrict__ w,
+              double *__restrict__ x, double *__restrict__ r, const gidx *__restrict__ off,
+              const gidx *__restrict__ idx, double *__restrict__ U, double *__restrict__ part,
+              unsigned *__restrict__ cnt) {
+  if (S[kDone] != 0.0) return;
+  const double alpha = S[kAlpha];
+  double rr = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    x[g] += alpha * p[g];
+    const double rg = r[g] - alpha * w[g];
+    r[g] = rg;
+    for (gidx q = off[g]; q < off[g + 1]; ++q) U[idx[q]] = rg;
+    rr += rg * rg;
+  }
+  red::block_reduce_store(rr, part + blockIdx.x);
+  if (!red::arrive_last(cnt)) return;
+  const double rrt = red::sum_partials(part, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double it = S[kIter] + 1.0;
+    S[kIter] = it;
+    S[kRr] = rrt;
+    if (rrt <= S[kTol2]) {
+      S[kDone] = 1.0;
+      S[kConvIt] = it;
+    } else if (!(rrt == rrt)) {
+      S[kDone] = 1.0;
+      S[kConvIt] = -it;
+    } else if (rrt < 0.25 * S[kBestRr]) {
+      S[kBestRr] = rrt;
+      S[kBestIt] = it;
+    } else if (S[kLearnOff] == 0.0 && it - S[kBestIt] >= S[kPatience]) {
+      S[kLearnOff] = 1.0;
+    }
+    S[kMlpSkip] = (S[kDone] != 0.0 || S[kLearnOff] != 0.0) ? 1.0 : 0.0;
+  }
+}
+
+constexpr int kRcpTable = 33;
+__constant__ float c_rcp[kRcpTable] = {
+    0.0f,        1.0f,        1.0f / 2,  1.0f / 3,  1.0f / 4,  1.0f / 5,  1.0f / 6,  1.0f / 7,  1.0f / 8,
+    1.0f / 9,    1.0f / 10,   1.0f / 11, 1.0f / 12, 1.0f / 13, 1.0f / 14, 1.0f / 15, 1.0f / 16, 1.0f / 17,
+    1.0f / 18,   1.0f / 19,   1.0f / 20, 1.0f / 21, 1.0f / 22, 1.0f / 23, 1.0f / 24, 1.0f / 25, 1.0f / 26,
+    1.0f / 27,   1.0f / 28,   1.0f / 29, 1.0f / 30, 1.0f / 31, 1.0f / 32};
+
+// z = D^-1 r + omega (sum of the local corrections c = scale_e Y_e of g) / multiplicity,
+// the correction summed in float; partial dots r.z and w.z.  When the
+// network is off (converged, or switched off by the patience test) z is the
+// Jacobi step.  The last block sets beta and rz, or, when the learned step is
+// not a descent direction (r.z <= 0), flags the iteration for lp_jacobi_fix.
+__global__ void __launch_bounds__(red::kThreads)
+    lp_precond(int64_t n, const gidx *__restrict__ off, const gidx *__restrict__ idx, const float *__restrict__ Y,
+               const float *__restrict__ scale, const double *__restrict__ dinv, const double *__restrict__ r,
+               const double *__restrict__ w, const uint8_t *__restrict__ mask, float omega, double *__restrict__ z,
+               double *__restrict__ part, unsigned *__restrict__ cnt, double *__restrict__ S) {
+  if (S[kDone] != 0.0) return;
+  const bool learned = S[kMlpSkip] == 0.0;
+  double rz = 0.0, wz = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double rg = r[g];
+    // the averaged correction in float: omega / multiplicity from a table
+    // (no int -> float conversion or division on the slow pipes)
+    float sc = 0.0f;
+    if (learned && !(mask && mask[g])) {
+      const gidx q0 = off[g], q1 = off[g + 1];
+      for (gidx q = q0; q < q1; ++q) {
+        const gidx l = idx[q];
+        sc += Y[l] * scale[l >> 9];  // 512 nodes per element at N = 7
+      }
+      const int k = q1 - q0;
+      sc *= omega * (k < kRcpTable ? c_rcp[k] : __frcp_rn((float)k));
+    }
+    const double zg = fma(dinv[g], rg, (double)sc);
+    z[g] = zg;
+    rz += rg * zg;
+    wz += w[g] * zg;
+  }
+  red::block_reduce_store(rz, part + blockIdx.x);
+  __syncthreads();
+  red::block_reduce_store(wz, part + kLpBlocks + blockIdx.x);
+  if (!red::arrive_last(cnt)) return;
+  const double RZ = red::sum_partials(part, gridDim.x);
+  const double WZ = red::sum_partials(part + kLpBlocks, gridDim.x);
+  if (threadIdx.x == 0) {
+    const bool jac = learned && !(RZ > 0.0);
+    S[kUseJac] = jac ? 1.0 : 0.0;
+    if (!jac) {
+      const double rz_old = S[kRz];
+      S[kBeta] = rz_old != 0.0 ? -S[kAlpha] * WZ / rz_old : 0.0;
+      S[kRz] = RZ;
+    }
+  }
+}
+
+// The safeguard: when lp_precond rejected the learned step, z = D^-1 r
+// (lp_direction recomputes it), rz = r.z, beta from w.z.  Otherwise a no-op.
+__global__ void __launch_bounds__(red::kThreads)
+    lp_jacobi_fix(int64_t n, const double *__restrict__ dinv, const double *__restrict__ r,
+                  const double *__restrict__ w, double *__restrict__ part, unsigned *__restrict__ cnt,
+                  double *__restrict__ S) {
+  if (S[kDone] != 0.0 || S[kUseJac] == 0.0) return;
+  double rz = 0.0, wz = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double zg = dinv[g] * r[g];
+    rz += r[g] * zg;
+    wz += w[g] * zg;
+  }
+  red::block_reduce_store(rz, part + blockIdx.x);
+  __syncthreads();
+  red::block_reduce_store(wz, part + kLpBlocks + blockIdx.x);
+  if (!red::arrive_last(cnt)) return;
+  const double RZ = red::sum_partials(part, gridDim.x);
+  const double WZ = red::sum_partials(part + kLpBlocks, gridDim.x);
+  if (threadIdx.x == 0) {
+    const double rz_old = S[kRz];
+    S[kBeta] = rz_old != 0.0 ? -S[kAlpha] * WZ / rz_old : 0.0;
+    S[kRz] = RZ;
+  }
 }
 
 inline unsigned gfor(int64_t n, int b = 256) {
@@ -252,6 +424,7 @@ struct ax_mlp {
   __nv_bfloat16 *H1 = nullptr, *H2 = nullptr, *dY = nullptr, *dZ1 = nullptr, *dZ2 = nullptr, *T1 = nullptr,
                 *T2 = nullptr;
   int64_t adam_t = 0;
+  int *derr = nullptr;  // device error word of the GEMM kernels (bounded waits that ran out)
   std::string err;
 };
 
@@ -272,6 +445,17 @@ ax_status mcuda(ax_mlp *m, cudaError_t e, const char *what) {
 }
 
 const int kRows[3] = {kHid, kHid, kOut}, kCols[3] = {kInPad, kHid, kHid};
+
+// After a synchronising point: AX_ETIMEOUT when a GEMM wait ran out (the
+// word is cleared for the next call).
+ax_status gemm_status(ax_mlp *m, const char *what) {
+  int h = 0;
+  if (cudaMemcpy(&h, m->derr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return AX_ECUDA;
+  if (!h) return AX_OK;
+  cudaMemset(m->derr, 0, sizeof(int));
+  m->err = std::string(what) + ": a tensor-core GEMM wait timed out (code " + std::to_string(h) + ")";
+  return AX_ETIMEOUT;
+}
 
 // splitmix64 (Steele, Lea, Flood 2014) and Box-Muller: deterministic host initialisation
 struct SplitMix {
@@ -319,22 +503,25 @@ cudaError_t ensure_cap(ax_mlp *m, int64_t rows) {
 }
 
 // forward of M rows of X (bf16 [M][kInPad]) -> m->Y (f32 [M][kOut])
-cudaError_t forward(ax_mlp *m, const __nv_bfloat16 *X, int64_t M, cudaStream_t s) {
+// (skip: optional device flag; when nonzero the three GEMMs do nothing;
+// keep_z: store the pre-activations for a backward pass)
+cudaError_t forward(ax_mlp *m, const __nv_bfloat16 *X, int64_t M, cudaStream_t s, const double *skip = nullptr,
+                    bool keep_z = false) {
   GemmOut o1;
-  o1.Cf = m->Z1; o1.Hb = m->H1; o1.bias = m->p + m->off[1]; o1.ldc = kHid;
-  cudaError_t e = gemm<kEpiGelu>((int)M, kHid, kInPad, X, kInPad, m->Wb[0], kInPad, o1, s);
+  o1.Cf = keep_z ? m->Z1 : nullptr; o1.Hb = m->H1; o1.bias = m->p + m->off[1]; o1.ldc = kHid; o1.skip = skip;
+  cudaError_t e = tc::gemm<kEpiGelu>((int)M, kHid, kInPad, X, m->Wb[0], o1, m->derr, s);
   GemmOut o2;
-  o2.Cf = m->Z2; o2.Hb = m->H2; o2.bias = m->p + m->off[3]; o2.ldc = kHid;
-  if (e == cudaSuccess) e = gemm<kEpiGelu>((int)M, kHid, kHid, m->H1, kHid, m->Wb[1], kHid, o2, s);
+  o2.Cf = keep_z ? m->Z2 : nullptr; o2.Hb = m->H2; o2.bias = m->p + m->off[3]; o2.ldc = kHid; o2.skip = skip;
+  if (e == cudaSuccess) e = tc::gemm<kEpiGelu>((int)M, kHid, kHid, m->H1, m->Wb[1], o2, m->derr, s);
   GemmOut o3;
-  o3.Cf = m->Y; o3.bias = m->p + m->off[5]; o3.ldc = kOut;
-  if (e == cudaSuccess) e = gemm<kEpiF32>((int)M, kOut, kHid, m->H2, kHid, m->Wb[2], kHid, o3, s);
+  o3.Cf = m->Y; o3.bias = m->p + m->off[5]; o3.ldc = kOut; o3.skip = skip;
+  if (e == cudaSuccess) e = tc::gemm<kEpiF32>((int)M, kOut, kHid, m->H2, m->Wb[2], o3, m->derr, s);
   return e;
 }
 
 // forward + backward of M rows (M a multiple of 32): gradients into m->g; loss partials in m->part
 cudaError_t forward_backward(ax_mlp *m, const __nv_bfloat16 *X, const float *T, int64_t M, cudaStream_t s) {
-  cudaError_t e = forward(m, X, M, s);
+  cudaError_t e = forward(m, X, M, s, nullptr, true);
   if (e != cudaSuccess) return e;
   loss_grad<<<1024, 256, 0, s>>>((int)M, kOut, m->Y, T, m->dY, m->part);
   const dim3 tb(32, 8);
@@ -347,27 +534,27 @@ cudaError_t forward_backward(ax_mlp *m, const __nv_bfloat16 *X, const float *T, 
   tr((int)M, kHid, m->H2, m->T2);
   GemmOut w3;
   w3.Cf = g + m->off[4]; w3.ldc = kHid;
-  e = gemm<kEpiF32>(kOut, kHid, (int)M, m->T1, (int)M, m->T2, (int)M, w3, s);
+  e = tc::gemm<kEpiF32>(kOut, kHid, (int)M, m->T1, m->T2, w3, m->derr, s);
   colsum_bf16<<<gfor(kOut), 256, 0, s>>>((int)M, kOut, m->dY, g + m->off[5]);
   GemmOut d2;
   d2.Hb = m->dZ2; d2.Zin = m->Z2; d2.ldc = kHid;
-  if (e == cudaSuccess) e = gemm<kEpiDGelu>((int)M, kHid, kOut, m->dY, kOut, m->WTb[2], kOut, d2, s);
+  if (e == cudaSuccess) e = tc::gemm<kEpiDGelu>((int)M, kHid, kOut, m->dY, m->WTb[2], d2, m->derr, s);
   // layer 2
   tr((int)M, kHid, m->dZ2, m->T1);
   tr((int)M, kHid, m->H1, m->T2);
   GemmOut w2;
   w2.Cf = g + m->off[2]; w2.ldc = kHid;
-  if (e == cudaSuccess) e = gemm<kEpiF32>(kHid, kHid, (int)M, m->T1, (int)M, m->T2, (int)M, w2, s);
+  if (e == cudaSuccess) e = tc::gemm<kEpiF32>(kHid, kHid, (int)M, m->T1, m->T2, w2, m->derr, s);
   colsum_bf16<<<gfor(kHid), 256, 0, s>>>((int)M, kHid, m->dZ2, g + m->off[3]);
   GemmOut d1;
   d1.Hb = m->dZ1; d1.Zin = m->Z1; d1.ldc = kHid;
-  if (e == cudaSuccess) e = gemm<kEpiDGelu>((int)M, kHid, kHid, m->dZ2, kHid, m->WTb[1], kHid, d1, s);
+  if (e == cudaSuccess) e = tc::gemm<kEpiDGelu>((int)M, kHid, kHid, m->dZ2, m->WTb[1], d1, m->derr, s);
   // layer 1
   tr((int)M, kHid, m->dZ1, m->T1);
   tr((int)M, kInPad, X, m->T2);
   GemmOut w1;
   w1.Cf = g + m->off[0]; w1.ldc = kInPad;
-  if (e == cudaSuccess) e = gemm<kEpiF32>(kHid, kInPad, (int)M, m->T1, (int)M, m->T2, (int)M, w1, s);
+  if (e == cudaSuccess) e = tc::gemm<kEpiF32>(kHid, kInPad, (int)M, m->T1, m->T2, w1, m->derr, s);
   colsum_bf16<<<gfor(kHid), 256, 0, s>>>((int)M, kHid, m->dZ1, g + m->off[1]);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
@@ -406,6 +593,9 @@ ax_status ax_mlp_create(ax_mlp **out, uint64_t seed, void *stream) {
       for (int c = 0; c < kCols[l]; ++c)
         h[m->off[2 * l] + (int64_t)r * kCols[l] + c] = (l == 0 && c >= kIn) ? 0.0f : (float)(sd * rng.normal());
   }
+  if (e == cudaSuccess) e = tc::gemm_init();
+  if (e == cudaSuccess) e = cudaMalloc(&m->derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->derr, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&m->p, sizeof(float) * o);
   if (e == cudaSuccess) e = cudaMalloc(&m->g, sizeof(float) * o);
   if (e == cudaSuccess) e = cudaMalloc(&m->am, sizeof(float) * o);
@@ -473,7 +663,7 @@ ax_status ax_mlp_grad(ax_mlp *m, const void *X_bf16, const float *T, int64_t M, 
   double acc = 0.0;
   for (float v : part) acc += v;
   *loss = (float)(0.5 * acc / ((double)M * kOut));
-  return AX_OK;
+  return gemm_status(m, "ax_mlp_grad");
 }
 
 ax_status ax_mlp_train(ax_mlp *m, const void *X_bf16, const float *T, int64_t n_samples, int epochs, int batch,
@@ -520,7 +710,7 @@ ax_status ax_mlp_train(ax_mlp *m, const void *X_bf16, const float *T, int64_t n_
   cudaFree(Xb);
   cudaFree(Tb);
   cudaFree(idx);
-  return e == cudaSuccess ? AX_OK : mcuda(m, e, "ax_mlp_train");
+  return e == cudaSuccess ? gemm_status(m, "ax_mlp_train") : mcuda(m, e, "ax_mlp_train");
 }
 
 }  // extern "C"
@@ -530,32 +720,63 @@ namespace {
 // Work buffers shared by ax_mlp_pairs and pcg_solve_learned.
 struct LearnWork {
   int64_t n = 0, nl = 0, E = 0;
-  double *r = nullptr, *w = nullptr, *Ul = nullptr, *Yl = nullptr, *dinv = nullptr, *diag_l = nullptr,
-         *scale = nullptr, *cl = nullptr, *part = nullptr;
+  double *r = nullptr, *w = nullptr, *z = nullptr, *p = nullptr, *bm = nullptr, *Ul = nullptr, *Yl = nullptr,
+         *dinv = nullptr, *part = nullptr, *S = nullptr, *hS = nullptr;
+  float *scale = nullptr;
+  unsigned *cnt = nullptr;
   __nv_bfloat16 *F = nullptr;
-  float *Y = nullptr;
   cudaError_t alloc(int64_t n_, int64_t nl_, int64_t E_) {
     n = n_;
     nl = nl_;
     E = E_;
     cudaError_t e = cudaMalloc(&r, sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&bm, sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMalloc(&dinv, sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMalloc(&Ul, sizeof(double) * nl);
     if (e == cudaSuccess) e = cudaMalloc(&Yl, sizeof(double) * nl);
-    if (e == cudaSuccess) e = cudaMalloc(&diag_l, sizeof(double) * nl);
-    if (e == cudaSuccess) e = cudaMalloc(&cl, sizeof(double) * nl);
-    if (e == cudaSuccess) e = cudaMalloc(&scale, sizeof(double) * E);
-    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 1024);
+    if (e == cudaSuccess) e = cudaMalloc(&scale, sizeof(float) * E);
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(double) * 4 * kLpBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(double) * kLpScalars);
+    if (e == cudaSuccess) e = cudaMemset(S, 0, sizeof(double) * kLpScalars);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMemset(cnt, 0, sizeof(unsigned) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&hS, sizeof(double) * kLpScalars);
     if (e == cudaSuccess) e = cudaMalloc(&F, sizeof(__nv_bfloat16) * E * kInPad);
-    if (e == cudaSuccess) e = cudaMalloc(&Y, sizeof(float) * E * kOut);
     return e;
   }
   void release() {
-    cudaFree(r); cudaFree(w); cudaFree(dinv); cudaFree(Ul); cudaFree(Yl); cudaFree(diag_l); cudaFree(cl);
-    cudaFree(scale); cudaFree(part); cudaFree(F); cudaFree(Y);
+    cudaFree(r); cudaFree(w); cudaFree(z); cudaFree(p); cudaFree(bm); cudaFree(dinv); cudaFree(Ul); cudaFree(Yl);
+    cudaFree(scale); cudaFree(part); cudaFree(S); cudaFree(cnt); cudaFreeHost(hS); cudaFree(F);
   }
 };
+
+void delete_learn(void *p) {
+  LearnWork *W = static_cast<LearnWork *>(p);
+  W->release();
+  delete W;
+}
+
+// The context's learned-solver work (kept between calls, freed with the context).
+cudaError_t learn_work(ax_ctx *c, LearnWork **out) {
+  Ctx &C = ax_ctx_core_mut(c);
+  LearnWork *W = static_cast<LearnWork *>(C.ws[Ctx::kWsLearn]);
+  if (!W) {
+    W = new (std::nothrow) LearnWork;
+    if (!W) return cudaErrorMemoryAllocation;
+    cudaError_t e = W->alloc(C.gs.n_global, C.gs.n_local, C.E);
+    if (e != cudaSuccess) {
+      delete_learn(W);
+      return e;
+    }
+    C.ws[Ctx::kWsLearn] = W;
+    C.ws_del[Ctx::kWsLearn] = delete_learn;
+  }
+  *out = W;
+  return cudaSuccess;
+}
 
 cudaError_t (*ax_launcher(int prec))(const AxArgs &) {
   switch (prec) {
@@ -588,29 +809,36 @@ cudaError_t jacobi_inverse(ax_ctx *c, LearnWork &W, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-double host_dot(LearnWork &W, const double *a, const double *b, int64_t n, cudaStream_t s, cudaError_t *err) {
-  std::vector<double> h(1024);
-  dot_d<<<1024, 256, 0, s>>>(n, a, b, W.part);
-  cudaError_t e = cudaMemcpyAsync(h.data(), W.part, sizeof(double) * 1024, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) *err = e;
-  double acc = 0.0;
-  for (double v : h) acc += v;
-  return acc;
+// The preconditioner on the current residual W.r: U = Q r, the network on
+// every element, z and beta (lp_precond).  skip: S[kMlpSkip].
+cudaError_t lp_apply(const ax_ctx *c, ax_mlp *m, LearnWork &W, double omega, bool scatter, cudaStream_t s) {
+  const GsPlan &P = ax_ctx_core(c).gs;
+  const int64_t E = ax_ctx_core(c).E, n = P.n_global;
+  const double *skip = W.S + kMlpSkip;
+  if (scatter) lp_scatter<<<gfor(n), 256, 0, s>>>(n, W.r, P.off, P.idx, W.Ul);
+  element_inputs<<<input_blocks(E), 32 * kInputWarps, 0, s>>>(E, nullptr, W.Ul, ax_ctx_vertices(c), W.F, W.scale, skip);
+  cudaError_t e = forward(m, W.F, E, s, skip);
+  if (e != cudaSuccess) return e;
+  lp_precond<<<kLpBlocks, red::kThreads, 0, s>>>(n, P.off, P.idx, m->Y, W.scale, W.dinv, W.r, W.w, P.mask,
+                                                 (float)omega, W.z, W.part, W.cnt + 3, W.S);
+  lp_jacobi_fix<<<kLpBlocks, red::kThreads, 0, s>>>(n, W.dinv, W.r, W.w, W.part + 2 * kLpBlocks, W.cnt + 3, W.S);
+  return cudaGetLastError();
 }
 
-// z = D^-1 r + omega Q^T(c) / multiplicity with c from the MLP on every element
-cudaError_t apply_learned(const ax_ctx *c, ax_mlp *m, LearnWork &W, const double *r, double *z, double omega,
-                          cudaStream_t s) {
+// One flexible-PCG iteration on stream s (x: the solution vector).
+cudaError_t lp_iteration(const ax_ctx *c, ax_mlp *m, LearnWork &W, double *x, double omega, cudaStream_t s) {
   const GsPlan &P = ax_ctx_core(c).gs;
-  const int64_t E = ax_ctx_core(c).E;
-  scatter_d<<<gfor(P.n_local), 256, 0, s>>>(P.n_local, P.gid, r, W.Ul);
-  element_inputs<<<(unsigned)E, 256, 0, s>>>(E, nullptr, W.Ul, ax_ctx_vertices(c), W.F, W.scale);
-  cudaError_t e = forward(m, W.F, E, s);
+  const int64_t n = P.n_global;
+  lp_direction<<<gfor(n), 256, 0, s>>>(n, W.S, W.z, W.r, W.dinv, W.p, P.off, P.idx, W.Ul);
+  AxArgs a = ax_ctx_args(c);
+  a.X = W.Ul;
+  a.Y = W.Yl;
+  a.stream = s;
+  cudaError_t e = ax_launcher(ax_ctx_core(c).prec)(a);
   if (e != cudaSuccess) return e;
-  element_correction<<<gfor(E * kOut), 256, 0, s>>>(E, m->Y, W.scale, W.cl);
-  precond_combine<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, P.off, P.idx, W.cl, W.dinv, r, P.mask, omega, z);
-  return cudaGetLastError();
+  lp_gather<<<kLpBlocks, red::kThreads, 0, s>>>(n, P.off, P.idx, W.Yl, W.w, P.mask, W.p, W.part, W.cnt, W.S);
+  lp_update<<<kLpBlocks, red::kThreads, 0, s>>>(n, W.S, W.p, W.w, x, W.r, P.off, P.idx, W.Ul, W.part, W.cnt + 1);
+  return lp_apply(c, m, W, omega, false, s);
 }
 
 }  // namespace
@@ -627,32 +855,24 @@ ax_status ax_mlp_pairs(ax_ctx *c, const double *b_global, const double *x_star, 
   if (!ax_launcher(C.prec)) return mfail(nullptr, AX_EUNSUPPORTED, "ax_mlp_pairs: needs an AX_FP64 or AX_F64DW context");
   if (n == 0) return AX_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  LearnWork W;
-  double *e_glob = nullptr, *el = nullptr, *dl = nullptr, *sc = nullptr;
-  cudaError_t e = W.alloc(C.gs.n_global, C.gs.n_local, C.E);
-  if (e == cudaSuccess) e = cudaMalloc(&e_glob, sizeof(double) * C.gs.n_global);
-  if (e == cudaSuccess) e = cudaMalloc(&el, sizeof(double) * C.gs.n_local);
-  if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(double) * C.gs.n_local);
-  if (e == cudaSuccess) e = cudaMalloc(&sc, sizeof(double) * n);
-  if (e == cudaSuccess) e = jacobi_inverse(c, W, s);
+  LearnWork *Wp = nullptr;
+  cudaError_t e = learn_work(c, &Wp);
+  if (e != cudaSuccess) return mcuda(nullptr, e, "ax_mlp_pairs");
+  LearnWork &W = *Wp;
+  if (n > C.E) return mfail(nullptr, AX_EINVAL, "ax_mlp_pairs: more samples than elements");
+  e = jacobi_inverse(c, W, s);
   if (e == cudaSuccess) e = apply_A(c, W, x_k, W.w, s);
   if (e == cudaSuccess) {
     const GsPlan &P = C.gs;
-    sub_d<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, b_global, W.w, W.r, P.mask);    // r = b - A x_k
-    sub_d<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, x_star, x_k, e_glob, P.mask);  // e = x* - x_k
+    sub_d<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, b_global, W.w, W.r, P.mask);  // r = b - A x_k
+    sub_d<<<gfor(P.n_global), 256, 0, s>>>(P.n_global, x_star, x_k, W.z, P.mask);    // e = x* - x_k
     scatter_d<<<gfor(P.n_local), 256, 0, s>>>(P.n_local, P.gid, W.r, W.Ul);
-    scatter_d<<<gfor(P.n_local), 256, 0, s>>>(P.n_local, P.gid, e_glob, el);
-    scatter_d<<<gfor(P.n_local), 256, 0, s>>>(P.n_local, P.gid, W.dinv, dl);
-    element_inputs<<<(unsigned)n, 256, 0, s>>>(n, elements, W.Ul, ax_ctx_vertices(c), (__nv_bfloat16 *)F_bf16, sc);
-    element_targets<<<(unsigned)n, 256, 0, s>>>(n, elements, el, dl, W.Ul, sc, T);
+    element_inputs<<<input_blocks(n), 32 * kInputWarps, 0, s>>>(n, elements, W.Ul, ax_ctx_vertices(c),
+                                                                (__nv_bfloat16 *)F_bf16, W.scale, nullptr);
+    element_targets<<<(unsigned)n, 256, 0, s>>>(n, elements, P.gid, W.z, W.dinv, W.Ul, W.scale, T);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  W.release();
-  cudaFree(e_glob);
-  cudaFree(el);
-  cudaFree(dl);
-  cudaFree(sc);
   return e == cudaSuccess ? AX_OK : mcuda(nullptr, e, "ax_mlp_pairs");
 }
 
@@ -669,99 +889,93 @@ ax_status pcg_solve_learned(ax_ctx *c, ax_mlp *m, const double *b_global, double
   cudaStream_t s = (cudaStream_t)stream;
   const GsPlan &P = C.gs;
   const int64_t n = P.n_global;
+  constexpr int kCheck = 16;   // iterations per graph launch (between host checks)
+  constexpr int kPatience = 200;
   *iters = 0;
   *relres = 0.0;
-  LearnWork W;
-  double *z = nullptr, *p = nullptr, *rold = nullptr, *bm = nullptr;
-  cudaError_t e = W.alloc(n, P.n_local, C.E);
-  if (e == cudaSuccess) e = ensure_cap(m, C.E);
-  if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&p, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&rold, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&bm, sizeof(double) * n);
+  LearnWork *Wp = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = learn_work(c, &Wp);
+  if (e != cudaSuccess) return mcuda(m, e, "pcg_solve_learned");
+  LearnWork &W = *Wp;
+  e = ensure_cap(m, C.E);
   if (e == cudaSuccess) e = jacobi_inverse(c, W, s);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   int conv = 0;
+  double bb = 0.0, rr = 0.0;
   if (e == cudaSuccess) {
-    // masked b and x; r = b - A x
+    // masked x; r = b - A x (masked); p = 0; ||b||, ||r||
     e = cudaMemsetAsync(W.w, 0, sizeof(double) * n, s);
-    sub_d<<<gfor(n), 256, 0, s>>>(n, b_global, W.w, bm, P.mask);
-    sub_d<<<gfor(n), 256, 0, s>>>(n, x, W.w, x, P.mask);
+    sub_d<<<gfor(n), 256, 0, s>>>(n, x, W.w, x, P.mask);  // x = 0 on Dirichlet nodes
     if (e == cudaSuccess) e = apply_A(c, W, x, W.w, s);
-    sub_d<<<gfor(n), 256, 0, s>>>(n, bm, W.w, W.r, P.mask);
-    const double bnorm = std::sqrt(host_dot(W, bm, bm, n, s, &e));
-    double rnorm = std::sqrt(host_dot(W, W.r, W.r, n, s, &e));
-    int it = 0;
-    if (bnorm == 0.0 || rnorm <= rtol * bnorm) conv = 1;
-    // preconditioner with safeguards: a learned step that is not a descent
-    // direction (r . z <= 0) is replaced by the Jacobi step; after the
-    // residual has failed to halve for `patience` iterations the solve falls
-    // back to Jacobi for good (then it is plain Jacobi-PCG).
-    const int patience = 200;
-    double best = rnorm;
-    int best_it = 0;
-    bool learned_on = true;
-    auto precond = [&](double &rz_out) {
-      if (learned_on) {
-        e = apply_learned(c, m, W, W.r, z, omega, s);
-        if (e != cudaSuccess) return;
-        rz_out = host_dot(W, W.r, z, n, s, &e);
-        if (rz_out > 0.0 && rz_out == rz_out) return;
-      }
-      jacobi_d<<<gfor(n), 256, 0, s>>>(n, W.dinv, W.r, z);
-      rz_out = host_dot(W, W.r, z, n, s, &e);
-    };
-    double rz = 0.0;
-    if (!conv && e == cudaSuccess) precond(rz);
-    if (!conv && e == cudaSuccess) e = cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-    while (!conv && e == cudaSuccess && it < maxit) {
-      e = apply_A(c, W, p, W.w, s);
+    lp_init<<<kLpBlocks, red::kThreads, 0, s>>>(n, b_global, W.w, W.bm, W.r, W.p, P.mask, rtol, (double)kPatience,
+                                                W.part, W.cnt + 2, W.S);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(W.hS, W.S, sizeof(double) * kLpScalars, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      bb = W.hS[kBb];
+      rr = W.hS[kRr];
+      if (bb == 0.0 || rr <= W.hS[kTol2]) conv = 1;
+    }
+  }
+  int it = 0;
+  if (e == cudaSuccess && !conv && maxit > 0) {
+    e = lp_apply(c, m, W, omega, true, s);  // z0, rz0 (beta = 0: p = z0)
+    if (e == cudaSuccess) e = cudaEventRecord(ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e == cudaSuccess && maxit >= kCheck) {
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      for (int q = 0; q < kCheck && e == cudaSuccess; ++q) e = lp_iteration(c, m, W, x, omega, cs);
+      const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = ec;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+    }
+    int issued = 0;
+    while (e == cudaSuccess && issued < maxit) {
+      const int block = (maxit - issued) < kCheck ? (maxit - issued) : kCheck;
+      if (block == kCheck)
+        e = cudaGraphLaunch(exec, cs);
+      else
+        for (int q = 0; q < block && e == cudaSuccess; ++q) e = lp_iteration(c, m, W, x, omega, cs);
+      issued += block;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(W.hS, W.S, sizeof(double) * kLpScalars, cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
       if (e != cudaSuccess) break;
-      const double pw = host_dot(W, p, W.w, n, s, &e);
-      const double alpha = pw != 0.0 ? rz / pw : 0.0;
-      axpy_d<<<gfor(n), 256, 0, s>>>(n, alpha, p, x);
-      e = cudaMemcpyAsync(rold, W.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-      axpy_d<<<gfor(n), 256, 0, s>>>(n, -alpha, W.w, W.r);
-      ++it;
-      rnorm = std::sqrt(host_dot(W, W.r, W.r, n, s, &e));
-      if (!(rnorm == rnorm)) break;
-      if (rnorm <= rtol * bnorm) {
-        conv = 1;
+      rr = W.hS[kRr];
+      it = issued;
+      if (W.hS[kDone] != 0.0) {
+        conv = W.hS[kConvIt] > 0.0;
+        it = (int)std::fabs(W.hS[kConvIt]);
         break;
       }
-      if (rnorm < 0.5 * best) {
-        best = rnorm;
-        best_it = it;
-      } else if (learned_on && it - best_it >= patience) {
-        learned_on = false;
-        *fell_back = 1;
-      }
-      double rz_new = 0.0;
-      if (e == cudaSuccess) precond(rz_new);
-      // flexible (Polak-Ribiere) beta = z . (r - r_old) / rz
-      sub_d<<<gfor(n), 256, 0, s>>>(n, W.r, rold, rold, nullptr);
-      const double zdr = host_dot(W, z, rold, n, s, &e);
-      const double beta = rz != 0.0 ? zdr / rz : 0.0;
-      rz = rz_new;
-      xpby_d<<<gfor(n), 256, 0, s>>>(n, z, beta, p);
     }
-    *iters = it;
-    *relres = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    *fell_back = W.hS[kLearnOff] != 0.0 ? 1 : 0;
+    const cudaError_t e2 = cudaEventRecord(ev, cs);
+    if (e2 == cudaSuccess) cudaStreamWaitEvent(s, ev, 0);
+    if (e == cudaSuccess) e = e2;
   }
+  *iters = it;
+  *relres = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  W.release();
-  cudaFree(z);
-  cudaFree(p);
-  cudaFree(rold);
-  cudaFree(bm);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (ev) cudaEventDestroy(ev);
+  if (cs) cudaStreamDestroy(cs);
   if (e != cudaSuccess) return mcuda(m, e, "pcg_solve_learned");
+  const ax_status gst = gemm_status(m, "pcg_solve_learned");
+  if (gst != AX_OK) return gst;
   if (!conv) return mfail(m, AX_ENOTCONV, "pcg_solve_learned: not converged");
   return AX_OK;
 }
 
 void ax_mlp_destroy(ax_mlp *m) {
   if (!m) return;
-  cudaFree(m->p); cudaFree(m->g); cudaFree(m->am); cudaFree(m->av);
+  cudaFree(m->p); cudaFree(m->g); cudaFree(m->am); cudaFree(m->av); cudaFree(m->derr);
   for (int l = 0; l < 3; ++l) {
     cudaFree(m->Wb[l]);
     cudaFree(m->WTb[l]);

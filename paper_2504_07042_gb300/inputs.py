@@ -153,7 +153,7 @@ def smooth_rhs(XYZ: np.ndarray, seed: int, order: int = 3) -> np.ndarray:
     """Random smooth source f(x) = sum_{a,b,c=1..order} c_abc sin(a pi x) sin(b pi y) sin(c pi z),
     c_abc ~ N(0,1) / (a^2 + b^2 + c^2), evaluated at node coordinates XYZ [E][3][n3]
     (rng seed `seed`; the training solves use seeds 100..299)."""
-    rng = np.random.default_rng(seed)
+    C = smooth_rhs_coeffs(seed, order)
     f = np.zeros(XYZ[:, 0].shape)
     sx = [np.sin(a * np.pi * XYZ[:, 0]) for a in range(1, order + 1)]
     sy = [np.sin(b * np.pi * XYZ[:, 1]) for b in range(1, order + 1)]
@@ -161,5 +161,16 @@ def smooth_rhs(XYZ: np.ndarray, seed: int, order: int = 3) -> np.ndarray:
     for a in range(order):
         for b in range(order):
             for c in range(order):
-                f += rng.standard_normal() / ((a + 1) ** 2 + (b + 1) ** 2 + (c + 1) ** 2) * sx[a] * sy[b] * sz[c]
+                f += C[a, b, c] * sx[a] * sy[b] * sz[c]
     return f
+
+
+def smooth_rhs_coeffs(seed: int, order: int = 3) -> np.ndarray:
+    """The coefficients c_abc of smooth_rhs (same draw order: a, then b, then c)."""
+    rng = np.random.default_rng(seed)
+    C = np.empty((order, order, order))
+    for a in range(order):
+        for b in range(order):
+            for c in range(order):
+                C[a, b, c] = rng.standard_normal() / ((a + 1) ** 2 + (b + 1) ** 2 + (c + 1) ** 2)
+    return C

@@ -108,8 +108,7 @@ def test_learned_pcg(ax, orc):
     Vd = torch.from_numpy(V).to(DEV)
     op = ax.Ax(Vd, N, "trilinear", "f64dw")
     op.gs_setup(torch.from_numpy(gid).to(DEV), ng, torch.from_numpy(mask).to(DEV))
-    lo = ax.Ax(Vd, N, "trilinear", "fp32")
-    F, T = learned.collect_pairs(op, lo, ng, seeds=range(100, 112), per_snapshot=n ** 3)
+    F, T = learned.collect_pairs(op, ng, seeds=range(100, 112), per_snapshot=n ** 3)
     assert F.shape[0] == 12 * 4 * n ** 3 and torch.isfinite(T).all()
     mlp = ax.AxMLP(seed=2)
     hist = mlp.ax_mlp_train(F, T, epochs=30, batch=512, lr=1e-3, seed=4)
