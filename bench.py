@@ -518,8 +518,10 @@ def run_sweep(ax, torch, dev, hbm, sm_mhz):
     stream = torch.cuda.current_stream()
     for N in (3, 5, 7, 9, 11, 15):
         for mesh, kinds in (("trilinear", ("stored", "trilinear", "partial")), ("parallelepiped", ("parallelepiped",))):
-            for prec in ("fp64", "f64dw", "fp32"):
+            for prec in ("fp64", "f64dw", "fp32", "tf32", "bf16", "fp16"):
                 for kind in kinds:
+                    if prec in ("tf32", "bf16", "fp16") and kind in ("stored", "partial"):
+                        continue  # tensor-core contractions: the recompute kinds only
                     op, X, Y, _ = _build_case(ax, torch, dev, N, kind, prec, mesh)
                     info = op.ax_query()
                     ms = _time_launches(torch, lambda: op.ax_local(X, Y, stream), 5, 2, stream)

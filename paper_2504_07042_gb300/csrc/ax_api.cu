@@ -73,12 +73,8 @@ ax::AxArgs make_args(ax_ctx *c, const void *X, void *Y, void *stream) {
 }
 
 cudaError_t run_ax(ax_ctx *c, const ax::AxArgs &a) {
-  switch (c->c.prec) {
-    case AX_FP64: return ax::launch_ax_fp64(a);
-    case AX_FP32: return ax::launch_ax_fp32(a);
-    case AX_F64DW: return ax::launch_ax_dw(a);
-    default: return cudaErrorNotSupported;
-  }
+  cudaError_t (*launch)(const ax::AxArgs &) = ax::ax_launcher_of(c->c.prec);
+  return launch ? launch(a) : cudaErrorNotSupported;
 }
 
 bool same_device(ax_ctx *c) {
@@ -89,6 +85,18 @@ bool same_device(ax_ctx *c) {
 }  // namespace
 
 namespace ax {
+cudaError_t (*ax_launcher_of(int prec))(const AxArgs &) {
+  switch (prec) {
+    case AX_FP64: return launch_ax_fp64;
+    case AX_FP32: return launch_ax_fp32;
+    case AX_F64DW: return launch_ax_dw;
+    case AX_TF32: return launch_ax_tf32;
+    case AX_BF16: return launch_ax_bf16;
+    case AX_FP16: return launch_ax_fp16;
+    default: return nullptr;
+  }
+}
+
 cudaError_t assembled_diag(ax_ctx *c, bool f64, const void **out, cudaStream_t s) {
   void **slot = f64 ? (void **)&c->c.diag64 : (void **)&c->c.diag32;
   if (*slot) {
@@ -147,8 +155,6 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
   if (E > 0 && !vertices) return fail(nullptr, AX_EINVAL, "ax_setup: vertices is NULL");
   if ((int)kind < 0 || (int)kind > 3) return fail(nullptr, AX_EINVAL, "ax_setup: bad geometry kind");
   if ((int)prec < 0 || (int)prec > 5) return fail(nullptr, AX_EINVAL, "ax_setup: bad precision");
-  if (prec == AX_TF32 || prec == AX_BF16 || prec == AX_FP16)
-    return fail(nullptr, AX_EUNSUPPORTED, "ax_setup: tensor-core precisions are not available in AxLocal contexts");
   const int64_t N1 = N + 1, n3 = N1 * N1 * N1;
   if (E > (int64_t)1 << 40 || E * n3 > ((int64_t)1 << 46))
     return fail(nullptr, AX_EINVAL, "ax_setup: problem too large");
@@ -169,8 +175,14 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
       case AX_FP64: e = ax::upload_tables_fp64(c->c.device); break;
       case AX_FP32: e = ax::upload_tables_fp32(c->c.device); break;
       case AX_F64DW: e = ax::upload_tables_dw(c->c.device); break;
+      // tensor-core contractions; the FP32 tables serve their factor export
+      case AX_TF32: e = ax::upload_tables_tf32(c->c.device); break;
+      case AX_BF16: e = ax::upload_tables_bf16(c->c.device); break;
+      case AX_FP16: e = ax::upload_tables_fp16(c->c.device); break;
       default: break;
     }
+    if (e == cudaSuccess && (prec == AX_TF32 || prec == AX_BF16 || prec == AX_FP16))
+      e = ax::upload_tables_fp32(c->c.device);
   }
   if (e != cudaSuccess) {
     ax_status st = cuda_fail(nullptr, e, "ax_setup: table upload");
@@ -276,7 +288,10 @@ ax_status ax_factors(ax_ctx *c, double *G_out, void *stream) {
   cudaError_t e;
   switch (c->c.prec) {
     case AX_FP64: e = ax::launch_factors_fp64(a, G_out); break;
-    case AX_FP32: e = ax::launch_factors_fp32(a, G_out); break;
+    case AX_FP32:
+    case AX_TF32:
+    case AX_BF16:
+    case AX_FP16: e = ax::launch_factors_fp32(a, G_out); break;  // FP32 geometry in every float32 context
     case AX_F64DW: e = ax::launch_factors_dw(a, G_out); break;
     default: return fail(c, AX_EUNSUPPORTED, "ax_factors: precision not supported");
   }
@@ -416,13 +431,7 @@ ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol
   cudaError_t e = cudaSuccess;
   if (precond == 1) e = ax::assembled_diag(c, f64, &diag_g, s);
   int conv = 0;
-  cudaError_t (*launch)(const ax::AxArgs &) = nullptr;
-  switch (c->c.prec) {
-    case AX_FP64: launch = ax::launch_ax_fp64; break;
-    case AX_FP32: launch = ax::launch_ax_fp32; break;
-    case AX_F64DW: launch = ax::launch_ax_dw; break;
-    default: break;
-  }
+  cudaError_t (*launch)(const ax::AxArgs &) = ax::ax_launcher_of(c->c.prec);
   if (e == cudaSuccess && !launch) e = cudaErrorNotSupported;
   if (e == cudaSuccess)
     e = ax::pcg_run(c->c, f64, make_args(c, nullptr, nullptr, stream), launch, b_global, x_global, diag_g, rtol,
@@ -454,11 +463,8 @@ ax_status pcg_solve_mixed(ax_ctx *hi, ax_ctx *lo, const double *b_global, double
   if (hi->c.gs.n_global == 0) return AX_OK;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t (*lh)(const ax::AxArgs &) = hi->c.prec == AX_FP64 ? ax::launch_ax_fp64 : ax::launch_ax_dw;
-  cudaError_t (*ll)(const ax::AxArgs &) = nullptr;
-  switch (lo->c.prec) {
-    case AX_FP32: ll = ax::launch_ax_fp32; break;
-    default: return fail(lo, AX_EUNSUPPORTED, "pcg_solve_mixed: lo precision has no AxLocal kernel");
-  }
+  cudaError_t (*ll)(const ax::AxArgs &) = ax::ax_launcher_of(lo->c.prec);
+  if (!ll) return fail(lo, AX_EUNSUPPORTED, "pcg_solve_mixed: lo precision has no AxLocal kernel");
   // the inner solve's Jacobi diagonal: the same mesh's operator, in float32
   const void *diag_g = nullptr;
   cudaError_t e = ax::assembled_diag(hi, false, &diag_g, s);

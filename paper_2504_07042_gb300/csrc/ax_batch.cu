@@ -285,14 +285,7 @@ void batch_release(ax_batch *b) {
   b->cs = nullptr;
 }
 
-cudaError_t (*launcher(ax_precision p))(const AxArgs &) {
-  switch (p) {
-    case AX_FP64: return launch_ax_fp64;
-    case AX_FP32: return launch_ax_fp32;
-    case AX_F64DW: return launch_ax_dw;
-    default: return nullptr;
-  }
-}
+cudaError_t (*launcher(ax_precision p))(const AxArgs &) { return ax_launcher_of((int)p); }
 
 AxArgs group_args(const ax_batch *b, const ax_batch::Group &g, const void *X, void *Y, cudaStream_t s) {
   const size_t w = f64_prec(b->prec) ? 8 : 4;

@@ -8,13 +8,17 @@ namespace ax {
 
 double pipe_ops_per_node(int N1, int kind, int prec) {
   const bool dwp = (prec == AX_F64DW);
+  const bool tc = (prec == AX_TF32 || prec == AX_BF16 || prec == AX_FP16);
   // cost of one scalar op in the arithmetic: add, multiply, multiply-accumulate, finalise
   const double add = dwp ? 11.0 : 1.0, mul = dwp ? 9.0 : 1.0, mac = dwp ? 12.0 : 1.0, fin = dwp ? 3.0 : 0.0;
   const double div = dwp ? 14.0 : 8.0;
   const double fma = dwp ? mul + add : 1.0;  // a*b + c: one FFMA/DFMA natively, a product and a sum in double-word
   // one even-odd fiber product of length N1: N1 prep adds, N1^2/2 macs, N1 finalisations, N1 post adds
   const double fiber = N1 * add + 0.5 * N1 * N1 * mac + N1 * fin + N1 * add;
-  double ops = 6.0 * fiber / N1;         // six contractions, each node in one fiber of each
+  // six contractions, each node in one fiber of each; on the tensor cores
+  // only the operand conversions stay on the FP32 pipe (one per operand for
+  // TF32, one per pair for the 16-bit formats)
+  double ops = tc ? (prec == AX_TF32 ? 6.0 : 3.0) : 6.0 * fiber / N1;
   ops += 3.0 * (3.0 * mac + fin);        // (r, s, t) = G (x0, x1, x2)
   ops += 2.0 * add;                      // Y accumulation of passes 3 and 4
   // trilinear geometry (Algorithm 2 with K = J^T J and det J as polynomials in t):

@@ -46,6 +46,25 @@ cudaError_t launch_dw_g5(const AxArgs &a, double *G_out);
 cudaError_t upload_tables_dw_g6(int device);
 cudaError_t launch_dw_g6(const AxArgs &a, double *G_out);
 
+cudaError_t upload_tables_tf32_g0(int device);
+cudaError_t launch_tf32_g0(const AxArgs &a);
+cudaError_t upload_tables_tf32_g1(int device);
+cudaError_t launch_tf32_g1(const AxArgs &a);
+cudaError_t upload_tables_tf32_g2(int device);
+cudaError_t launch_tf32_g2(const AxArgs &a);
+cudaError_t upload_tables_bf16_g0(int device);
+cudaError_t launch_bf16_g0(const AxArgs &a);
+cudaError_t upload_tables_bf16_g1(int device);
+cudaError_t launch_bf16_g1(const AxArgs &a);
+cudaError_t upload_tables_bf16_g2(int device);
+cudaError_t launch_bf16_g2(const AxArgs &a);
+cudaError_t upload_tables_fp16_g0(int device);
+cudaError_t launch_fp16_g0(const AxArgs &a);
+cudaError_t upload_tables_fp16_g1(int device);
+cudaError_t launch_fp16_g1(const AxArgs &a);
+cudaError_t upload_tables_fp16_g2(int device);
+cudaError_t launch_fp16_g2(const AxArgs &a);
+
 static int group_of(int N) {
   switch (N) {
     case 1: return 0;
@@ -150,5 +169,53 @@ cudaError_t upload_tables_dw(int device) {
 
 cudaError_t launch_ax_dw(const AxArgs &a) { return launch_dw(a, nullptr); }
 cudaError_t launch_factors_dw(const AxArgs &a, double *G_out) { return launch_dw(a, G_out); }
+
+// tensor-core contraction kernels: order groups {1..5}, {6..9}, {10..15}
+static int tc_group(int N) { return N >= 1 && N <= 5 ? 0 : (N >= 6 && N <= 9 ? 1 : (N >= 10 && N <= 15 ? 2 : -1)); }
+
+cudaError_t launch_ax_tf32(const AxArgs &a) {
+  switch (tc_group(a.N)) {
+    case 0: return launch_tf32_g0(a);
+    case 1: return launch_tf32_g1(a);
+    case 2: return launch_tf32_g2(a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t upload_tables_tf32(int device) {
+  cudaError_t e = upload_tables_tf32_g0(device);
+  if (e == cudaSuccess) e = upload_tables_tf32_g1(device);
+  if (e == cudaSuccess) e = upload_tables_tf32_g2(device);
+  return e;
+}
+
+cudaError_t launch_ax_bf16(const AxArgs &a) {
+  switch (tc_group(a.N)) {
+    case 0: return launch_bf16_g0(a);
+    case 1: return launch_bf16_g1(a);
+    case 2: return launch_bf16_g2(a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t upload_tables_bf16(int device) {
+  cudaError_t e = upload_tables_bf16_g0(device);
+  if (e == cudaSuccess) e = upload_tables_bf16_g1(device);
+  if (e == cudaSuccess) e = upload_tables_bf16_g2(device);
+  return e;
+}
+
+cudaError_t launch_ax_fp16(const AxArgs &a) {
+  switch (tc_group(a.N)) {
+    case 0: return launch_fp16_g0(a);
+    case 1: return launch_fp16_g1(a);
+    case 2: return launch_fp16_g2(a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t upload_tables_fp16(int device) {
+  cudaError_t e = upload_tables_fp16_g0(device);
+  if (e == cudaSuccess) e = upload_tables_fp16_g1(device);
+  if (e == cudaSuccess) e = upload_tables_fp16_g2(device);
+  return e;
+}
 
 }  // namespace ax

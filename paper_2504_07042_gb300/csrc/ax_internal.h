@@ -91,6 +91,15 @@ struct AxArgs {
 cudaError_t launch_ax_fp64(const AxArgs &a);
 cudaError_t launch_ax_fp32(const AxArgs &a);
 cudaError_t launch_ax_dw(const AxArgs &a);
+// tensor-core contractions (TF32, BF16, FP16 operands; FP32 accumulation, io and geometry)
+cudaError_t launch_ax_tf32(const AxArgs &a);
+cudaError_t launch_ax_bf16(const AxArgs &a);
+cudaError_t launch_ax_fp16(const AxArgs &a);
+cudaError_t upload_tables_tf32(int device);
+cudaError_t upload_tables_bf16(int device);
+cudaError_t upload_tables_fp16(int device);
+// AxLocal launcher of a precision (nullptr if none)
+cudaError_t (*ax_launcher_of(int prec))(const AxArgs &);
 
 // Factor export through the kernel's own geometry code (G_out [E][7][n3] float64).
 cudaError_t launch_factors_fp64(const AxArgs &a, double *G_out);

@@ -778,12 +778,9 @@ cudaError_t learn_work(ax_ctx *c, LearnWork **out) {
   return cudaSuccess;
 }
 
+// the learned solver runs FP64-accurate operators only
 cudaError_t (*ax_launcher(int prec))(const AxArgs &) {
-  switch (prec) {
-    case AX_FP64: return launch_ax_fp64;
-    case AX_F64DW: return launch_ax_dw;
-    default: return nullptr;
-  }
+  return (prec == AX_FP64 || prec == AX_F64DW) ? ax_launcher_of(prec) : nullptr;
 }
 
 // w = A x (assembled, masked), through the local vectors of W

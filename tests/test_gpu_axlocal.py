@@ -4,7 +4,8 @@ CPU oracle, through the C ABI.
 Bar: relative max-norm ||Y_gpu - Y_oracle||_inf / ||Y_oracle||_inf <= 1e-12 for
 the float64 precisions (native FP64 and double-word), the tolerance the
 FP64 requirement states; FP32 kernels are held to 2e-5 (FP32 rounding of
-about 2N1+10 accumulated terms, eps_32 = 6e-8, with margin).
+about 2N1+10 accumulated terms, eps_32 = 6e-8, with margin); the tensor-core
+contraction precisions to 4 u of their operand format.
 """
 import numpy as np
 import pytest
@@ -15,7 +16,11 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "f64dw": 1e-12, "fp32": 2e-5}
+# Tensor-core precisions round each contraction operand once to the format
+# (unit roundoff u = 2^-11 for TF32 and FP16, 2^-8 for BF16) and accumulate in
+# FP32: the measured error is 1-2 u; the bar is 4 u.
+TOL = {"fp64": 1e-12, "f64dw": 1e-12, "fp32": 2e-5, "tf32": 4 * 2.0 ** -11, "bf16": 4 * 2.0 ** -8,
+       "fp16": 4 * 2.0 ** -11}
 KINDS = ["stored", "trilinear", "parallelepiped", "partial"]
 
 
@@ -74,6 +79,32 @@ def test_every_order_ragged_mesh(ax, orc, kind, prec, N):
     Yref, _ = orc.axlocal_vertices(V, X, N)
     Y = _run(ax, V, X, N, kind, prec)
     assert _relerr(Y, Yref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
+@pytest.mark.parametrize("kind", KINDS)
+def test_tensor_core_precisions_c1(ax, orc, kind, prec):
+    # the contractions on the tensor cores; error stated against the FP64 oracle
+    V = _mesh(kind, 8, 8, 8)
+    X = inputs.element_vectors(V.shape[0], 7, seed=1)
+    Yref, _ = orc.axlocal_vertices(V, X, 7)
+    Y = _run(ax, V, X, 7, kind, prec)
+    err = _relerr(Y, Yref)
+    print("%s %s relerr %.3e" % (prec, kind, err))
+    assert err <= TOL[prec]
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
+@pytest.mark.parametrize("kind", ["trilinear", "parallelepiped"])
+def test_tensor_core_every_order(ax, orc, kind, prec, N):
+    V = _mesh(kind, 3, 2, 2)
+    X = inputs.element_vectors(V.shape[0], N, seed=7 + N)
+    Yref, _ = orc.axlocal_vertices(V, X, N)
+    Y = _run(ax, V, X, N, kind, prec)
+    err = _relerr(Y, Yref)
+    print("%s %s N=%d relerr %.3e" % (prec, kind, N, err))
+    assert err <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "f64dw"])

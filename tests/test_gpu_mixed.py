@@ -21,11 +21,11 @@ def ax():
     return _ax
 
 
-def _pair(ax, V, N, kind, hi_prec, gid, ng, mask):
+def _pair(ax, V, N, kind, hi_prec, gid, ng, mask, lo_prec="fp32"):
     Vd = torch.from_numpy(V).to(DEV)
     hi = ax.Ax(Vd, N, kind, hi_prec)
     hi.gs_setup(torch.from_numpy(gid).to(DEV), ng, torch.from_numpy(mask).to(DEV))
-    lo = ax.Ax(Vd, N, kind, "fp32")
+    lo = ax.Ax(Vd, N, kind, lo_prec)
     return hi, lo
 
 
@@ -70,6 +70,27 @@ def test_mixed_c3_to_1e10(ax):
     assert st == ax.AX_OK
     x = torch.zeros(ng, dtype=torch.float64, device=DEV)
     outer, inner, rr, st = hi.pcg_solve_mixed(lo, b, x, rtol=1e-10, inner_rtol=1e-3)
+    assert st == ax.AX_OK and rr <= 1e-10
+    diff = float((x - x64).abs().max()) / float(x64.abs().max())
+    assert diff < 1e-8
+
+
+@pytest.mark.parametrize("lo_prec", ["tf32", "bf16", "fp16"])
+def test_mixed_tensor_core_inner_c3(ax, lo_prec):
+    # inner CG with tensor-core contractions (FP32 accumulation), FP64 refinement to 1e-10:
+    # the refinement removes the inner operator's error; the answer matches FP64 PCG
+    N, n = 7, 16
+    V = inputs.box_vertices(n, n, n)
+    gid, ng = inputs.box_global_ids(n, n, n, N)
+    mask = inputs.box_boundary_mask(n, n, n, N)
+    hi, lo = _pair(ax, V, N, "trilinear", "f64dw", gid, ng, mask, lo_prec)
+    b, u = _rhs_gpu(hi, V, N, ng)
+    x64 = torch.zeros(ng, dtype=torch.float64, device=DEV)
+    it, rr64, st = hi.pcg_solve(b, x64, rtol=1e-10, maxit=10000, precond=1)
+    assert st == ax.AX_OK
+    x = torch.zeros(ng, dtype=torch.float64, device=DEV)
+    outer, inner, rr, st = hi.pcg_solve_mixed(lo, b, x, rtol=1e-10, inner_rtol=1e-2, max_outer=100)
+    print("%s: outer %d inner %d relres %.2e" % (lo_prec, outer, inner, rr))
     assert st == ax.AX_OK and rr <= 1e-10
     diff = float((x - x64).abs().max()) / float(x64.abs().max())
     assert diff < 1e-8
