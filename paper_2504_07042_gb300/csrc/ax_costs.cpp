@@ -29,13 +29,26 @@ double pipe_ops_per_node(int N1, int kind, int prec) {
   const double coeffs = 13.0 * dot3 + 3.0 * add, det_coeffs = 6.0 * det2 + 4.0 * dot3 + add;
   const double quad = 2.0 * fma, lin = fma;
   const double knode = 3.0 * quad + 2.0 * lin, adj = 6.0 * det2, scale = 3.0 * mul;
+  // FP64 shares the element terms (E0/E1 per s-point, F0/F1 per r-point, the
+  // t-edges and K00/K11 coefficients) among the element's threads: 2 N1 + 1
+  // producers per element instead of every thread
+  const bool share = (prec == AX_FP64);
+  const double n3 = (double)N1 * N1 * N1;
+  const double j2 = 3.0 * (4.0 * mac + fin) + 12.0 * mul;
+  const double own = j2 + 4.0 * dot3 + add + 4.0 * dot3 + dot3;  // J2, K01, K02, K12, K22
+  const double item = 12.0 * add + 6.0 * (2.0 * add + mul + fma) + 3.0 * dot3 + add + 4.0 * add;
+  const double shared_terms = (2.0 * N1 * item + 12.0 * add) / n3;
   switch (kind) {
     case AX_GEOM_STORED: break;
     case AX_GEOM_PARALLELEPIPED: ops += mul + 3.0 * mul; break;
     case AX_GEOM_TRILINEAR:
-      ops += knode + quad + adj + mul + div + scale + (prologue + coeffs + det_coeffs) / N1;
+      ops += knode + quad + adj + mul + div + scale;
+      ops += share ? (own + det_coeffs) / N1 + shared_terms : (prologue + coeffs + det_coeffs) / N1;
       break;
-    case AX_GEOM_TRILINEAR_PARTIAL: ops += knode + adj + scale + (prologue + coeffs) / N1; break;
+    case AX_GEOM_TRILINEAR_PARTIAL:
+      ops += knode + adj + scale;
+      ops += share ? own / N1 + shared_terms : (prologue + coeffs) / N1;
+      break;
   }
   return ops;
 }
