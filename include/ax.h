@@ -62,9 +62,12 @@ typedef enum {
 typedef enum {
   AX_FP64 = 0,  /* X, Y float64; native FP64 arithmetic */
   AX_FP32 = 1,  /* X, Y float32; FP32 arithmetic */
-  AX_TF32 = 2,  /* X, Y float32; contractions on tensor cores in TF32, FP32 accumulate */
-  AX_BF16 = 3,  /* X, Y float32; contractions on tensor cores in BF16, FP32 accumulate */
-  AX_FP16 = 4,  /* X, Y float32; contractions on tensor cores in FP16, FP32 accumulate */
+  AX_TF32 = 2,  /* X, Y float32; the six contractions on tensor cores (mma.sync m16n8k8) with TF32
+                   operands and FP32 accumulation; geometry and G x in FP32 (error about 1-2 u,
+                   u = 2^-11, against the FP64 result) */
+  AX_BF16 = 3,  /* as AX_TF32 with BF16 operands (u = 2^-8) */
+  AX_FP16 = 4,  /* as AX_TF32 with FP16 operands (u = 2^-11; inputs must stay inside FP16's range,
+                   which the mixed-precision solver's scaling by ||r||_inf ensures) */
   AX_F64DW = 5  /* X, Y float64; arithmetic in double-word FP32 pairs (about 47 bits) on the
                    FP32 pipe; same results as AX_FP64 to ~1e-13 relative max-norm */
 } ax_precision;
@@ -128,8 +131,10 @@ ax_status ax_node_coords(ax_ctx *c, double *XYZ_out, void *stream);
  *   dirichlet_mask: device, [n_global] uint8 (1 = homogeneous Dirichlet node,
  *   removed from the assembled system) or NULL.
  * Builds, once, a CSR of the local copies of every global node in increasing
- * local order (so every gather is a fixed-order, deterministic sum).
- * Synchronises the stream.  AX_EINVAL if an id is out of range. */
+ * local order (so every gather is a fixed-order, deterministic sum), with
+ * 32-bit indices: AX_ERANGE if E*n3 or n_global exceeds 2^31 - 1.
+ * Synchronises the stream.  AX_EINVAL if an id is out of range.  Frees the
+ * context's solver workspaces and cached diagonal (they depend on the plan). */
 ax_status gs_setup(ax_ctx *c, const int64_t *global_id, int64_t n_global, const uint8_t *dirichlet_mask,
                    void *stream);
 
@@ -158,8 +163,15 @@ ax_status ax_diag(ax_ctx *c, void *diag_local, void *stream);
  *   solution.  precond: 0 = none, 1 = Jacobi (assembled diagonal).
  *   Stops when ||r||_2 <= rtol ||b||_2 or after maxit iterations
  *   (AX_ENOTCONV).  *iters and *relres (host) report the outcome.
- * Allocates its work vectors per call; reads one scalar per iteration to
- * the host (the call synchronises). */
+ * One iteration is four kernels (direction + scatter, AxLocal, gather + p.w
+ * with alpha, update + r.z, r.r with the convergence test and beta); every
+ * scalar stays on the device and the grid-level sums are finished in the
+ * producing kernel in a fixed order (deterministic).  Blocks of 16
+ * iterations run as one CUDA graph on a private stream, ordered after and
+ * before `stream` by events; the host reads the scalars once per block.
+ * The work vectors, the stream and the graph are kept in the context for
+ * the next call (released by gs_setup and ax_destroy); the assembled
+ * Jacobi diagonal is computed at the first call and kept.  Synchronises. */
 ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol, int maxit, int precond, int *iters,
                     double *relres, void *stream);
 
@@ -168,7 +180,9 @@ ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol
  * paper names as future work, Sec. 7).
  *   hi: context with AX_FP64 or AX_F64DW and gs_setup done; computes the
  *       residual r = b - A x in FP64-accurate arithmetic each outer step.
- *   lo: context of the same mesh (same E, N, vertices) with AX_FP32; runs
+ *   lo: context of the same mesh (same E, N, vertices) with a float32
+ *       precision (AX_FP32, or AX_TF32 / AX_BF16 / AX_FP16 for tensor-core
+ *       contractions in the inner operator); runs
  *       the inner solve A d = r / ||r||_inf to inner_rtol (at most max_inner
  *       iterations); x += ||r||_inf d.
  *   b_global, x_global: device float64 [n_global]; x is the initial guess.
@@ -236,9 +250,11 @@ void ax_batch_destroy(ax_batch *b);
 
 /* ------------------------------------------------------------------------
  * Learned preconditioner (order N = 7 elements): a per-element MLP
- * 536 -> 512 (GELU) -> 512 (GELU) -> 512, BF16 tensor-core GEMMs with FP32
- * accumulation, FP32 master weights, Adam.  The paper has no counterpart;
- * the MLP corrects the Jacobi step of a flexible CG.
+ * 536 -> 512 (GELU) -> 512 (GELU) -> 512, BF16 GEMMs on the tcgen05 tensor
+ * cores (TMA-fed, FP32 accumulation in tensor memory, fused bias/GELU
+ * epilogues), FP32 master weights, Adam.  The paper has no counterpart;
+ * the MLP corrects the Jacobi step of a flexible CG.  Calls that
+ * synchronise return AX_ETIMEOUT if a GEMM's bounded wait gave up.
  * Element input (536 = 512 + 24): the element's local residual divided by
  * s_e = max |r_e|, and its vertex coordinates relative to vertex 0 divided by
  * h_e = |v1 - v0|; inputs are padded to 544 columns (zeros) in bf16.
@@ -288,7 +304,10 @@ ax_status ax_mlp_pairs(ax_ctx *c, const double *b_global, const double *x_star, 
  * replaced by the Jacobi step; if the residual has not halved for 200
  * iterations the solve falls back to Jacobi-PCG for the rest (*fell_back = 1).
  * Stops when ||r|| <= rtol ||b|| (AX_OK) or after maxit iterations
- * (AX_ENOTCONV).  Synchronises. */
+ * (AX_ENOTCONV).  Every scalar stays on the device (alpha, beta, the
+ * safeguard and the patience test are decided by the last block of the
+ * kernel that produces their sums); blocks of 16 iterations run as one CUDA
+ * graph; the work vectors are kept in the context.  Synchronises. */
 ax_status pcg_solve_learned(ax_ctx *c, ax_mlp *m, const double *b_global, double *x_global, double rtol, int maxit,
                             double omega, int *iters, double *relres, int *fell_back, void *stream);
 

@@ -157,11 +157,33 @@ __device__ __forceinline__ void contract(const typename P::C *__restrict__ eo, c
   }
 }
 
-template <int N1, int EM = 1>
+// Elements per CTA for F threads per element: at least 128 threads, and
+// among up to about four times that many elements (at most 512 threads) the
+// count that leaves the fewest idle lanes in the last warp (N1 = 6: 7
+// elements = 252 threads instead of 3 = 108 threads in four warps).
+__host__ __device__ constexpr int idle_lanes_permille(int t) { return ((t + 31) / 32 * 32 - t) * 1000 / ((t + 31) / 32 * 32); }
+__host__ __device__ constexpr int pick_epb(int F) {
+  int base = F >= 128 ? 1 : 128 / F, best = base, bw = idle_lanes_permille(F * base);
+  for (int e = base + 1; e <= 4 * base + 3 && F * e <= 512; ++e)
+    if (idle_lanes_permille(F * e) < bw) {
+      best = e;
+      bw = idle_lanes_permille(F * e);
+    }
+  return best;
+}
+
+// FILL: pick_epb; otherwise the plain 128-thread rule.  Measured on GB300:
+// filling the warps pays for the recompute kinds in 8-byte arithmetic
+// (double-word, FP64) and for FP32 at N1 = 6; the stored kind and FP32 at
+// N1 = 10, 12 run faster with the smaller CTAs (more of them per SM).
+template <class P, int N1, int KIND>
+constexpr bool kFillWarps = KIND != AX_GEOM_STORED && (sizeof(typename P::S) == 8 || N1 == 6);
+
+template <int N1, int EM = 1, bool FILL = false>
 struct Shape {
   static constexpr int n3 = N1 * N1 * N1;
   static constexpr int F = N1 * N1;  // fibers (threads) per element
-  static constexpr int EPB = EM * ((F >= 128) ? 1 : (128 / F));  // elements per CTA (EM: tile variant)
+  static constexpr int EPB = EM * (FILL ? pick_epb(F) : (F >= 128 ? 1 : 128 / F));  // elements per CTA (EM: tile variant)
   static constexpr int threads = F * EPB;
   static constexpr int P = N1 + 1;            // padded row
   static constexpr int ES = N1 * N1 * P;      // padded element size (words)
@@ -407,10 +429,10 @@ struct GeoWords {
 //   c_eoD / c_eoDT: even-odd blocks of D and D^T, c_w, c_x: weights, points.
 // ---------------------------------------------------------------------------
 template <class P, int N1, int KIND, int EM>
-__global__ void __launch_bounds__(Shape<N1, EM>::threads)
+__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads)
     ax_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
                     const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y) {
-  using Sh = Shape<N1, EM>;
+  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
   using V = typename P::V;
   using S = typename P::S;
   constexpr int n3 = Sh::n3, EPB = Sh::EPB, ES = Sh::ES;
@@ -481,41 +503,6 @@ __global__ void __launch_bounds__(Shape<N1, EM>::threads)
 #pragma unroll
     for (int n = 0; n < N1; ++n) dst[base + n * stride] = P::st(fout[n]);
   };
-  if constexpr (P::kRoll) {
-#pragma unroll 1
-    for (int ph = 0; ph < 3; ++ph) forward(ph);
-  } else {
-#pragma unroll
-    for (int ph = 0; ph < 3; ++ph) forward(ph);
-  }
-  __syncthreads();
-  {
-    // thread (i, j) = (qa, qb): geometry and G x along its own t-fiber
-    const int i = qa, j = qb;
-    Geometry<P, N1, KIND> gm;
-    gm.prologue(sgeo[z], sterm[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
-                (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
-    auto node = [&](int k) {
-      const int sidx = ft + k * str_t;
-      const V xv[3] = {P::ld(r_e + sidx), P::ld(s_e + sidx), P::ld(x_e + sidx)};
-      V o3[3];
-      if (live) {
-        gm.apply(i + j * N1 + k * N1 * N1, P::cst(cx + k), P::cst(cw + k), xv, o3);
-      } else {
-        o3[0] = o3[1] = o3[2] = P::lit(0.0);
-      }
-      r_e[sidx] = P::st(o3[0]);
-      s_e[sidx] = P::st(o3[1]);
-      x_e[sidx] = P::st(o3[2]);
-    };
-    if constexpr (P::kRoll) {
-#pragma unroll 1
-      for (int k = 0; k < N1; ++k) node(k);
-    } else {
-#pragma unroll
-      for (int k = 0; k < N1; ++k) node(k);
-    }
-  }
   auto transposed = [&](int ph) {
     if (ph >= 4) __syncthreads();  // ph 4: all r, s written; ph 5: Y updates of ph 4 done
     const S *src = ph == 3 ? x_e : (ph == 4 ? r_e : s_e);
@@ -536,12 +523,76 @@ __global__ void __launch_bounds__(Shape<N1, EM>::threads)
   };
   if constexpr (P::kRoll) {
 #pragma unroll 1
-    for (int ph = 3; ph < 6; ++ph) transposed(ph);
-  } else {
-#pragma unroll
-    for (int ph = 3; ph < 6; ++ph) transposed(ph);
-  }
+    for (int ph = 0; ph < 3; ++ph) forward(ph);
   __syncthreads();
+  {
+    // thread (i, j) = (qa, qb): geometry and G x along its own t-fiber
+    const int i = qa, j = qb;
+    Geometry<P, N1, KIND> gm;
+    gm.prologue(sgeo[z], sterm[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+                (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
+    auto node = [&](int k) {
+      const int sidx = ft + k * str_t;
+      const V xv[3] = {P::ld(r_e + sidx), P::ld(s_e + sidx), P::ld(x_e + sidx)};
+      V o3[3];
+      if (live) {
+        gm.apply(i + j * N1 + k * N1 * N1, P::cst(cx + k), P::cst(cw + k), xv, o3);
+      } else {
+        o3[0] = o3[1] = o3[2] = P::lit(0.0);
+      }
+      r_e[sidx] = P::st(o3[0]);
+      s_e[sidx] = P::st(o3[1]);
+      x_e[sidx] = P::st(o3[2]);
+    };
+#pragma unroll 1
+    for (int k = 0; k < N1; ++k) node(k);
+  }
+#pragma unroll 1
+    for (int ph = 3; ph < 6; ++ph) transposed(ph);
+  __syncthreads();
+  } else {
+    // Short code (native arithmetic): the thread's own t-fiber stays in
+    // registers from D_t x through the geometry to D_t^T t, so x is never
+    // overwritten before the transposed passes (one barrier fewer) and the
+    // t values make no shared-memory round trips.
+    forward(0);
+    forward(1);
+    V tf[N1];
+    {
+      V fin_[N1];
+#pragma unroll
+      for (int n = 0; n < N1; ++n) fin_[n] = P::ld(x_e + ft + n * str_t);
+      contract<P, N1>(eoD, fin_, tf);
+    }
+    __syncthreads();  // every r/s fiber product is in B0, B1
+    {
+      const int i = qa, j = qb;
+      Geometry<P, N1, KIND> gm;
+      gm.prologue(sgeo[z], sterm[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+                  (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const int sidx = ft + k * str_t;
+        const V xv[3] = {P::ld(r_e + sidx), P::ld(s_e + sidx), tf[k]};
+        V o3[3];
+        if (live) {
+          gm.apply(i + j * N1 + k * N1 * N1, P::cst(cx + k), P::cst(cw + k), xv, o3);
+        } else {
+          o3[0] = o3[1] = o3[2] = P::lit(0.0);
+        }
+        r_e[sidx] = P::st(o3[0]);
+        s_e[sidx] = P::st(o3[1]);
+        tf[k] = o3[2];
+      }
+      V yt[N1];
+      contract<P, N1>(eoDT, tf, yt);
+#pragma unroll
+      for (int n = 0; n < N1; ++n) x_e[ft + n * str_t] = P::st(yt[n]);
+    }
+#pragma unroll
+    for (int ph = 4; ph < 6; ++ph) transposed(ph);
+    __syncthreads();
+  }
 
   // pass 5: Y to HBM
   for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
@@ -556,10 +607,10 @@ __global__ void __launch_bounds__(Shape<N1, EM>::threads)
 
 // Factor export through the same geometry code: G_out [E][7][n3] float64.
 template <class P, int N1, int KIND>
-__global__ void __launch_bounds__(Shape<N1>::threads)
+__global__ void __launch_bounds__(Shape<N1, 1, kFillWarps<P, N1, KIND>>::threads)
     factors_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
                          double *__restrict__ G) {
-  using Sh = Shape<N1>;
+  using Sh = Shape<N1, 1, kFillWarps<P, N1, KIND>>;
   using V = typename P::V;
   using S = typename P::S;
   constexpr int n3 = Sh::n3, EPB = Sh::EPB;
@@ -599,14 +650,16 @@ __global__ void __launch_bounds__(Shape<N1>::threads)
 
 template <class P, int N1, int KIND, int EM>
 cudaError_t launch_ax_em(const AxArgs &a) {
-  using Sh = Shape<N1, EM>;
+  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
   const int64_t nblk = (a.E + Sh::EPB - 1) / Sh::EPB;
   if (nblk <= 0) return cudaSuccess;
   int64_t grid = a.grid > 0 && a.grid < nblk ? a.grid : nblk;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
   const size_t smem = (size_t)3 * Sh::EPB * Sh::ES * sizeof(typename P::S);
-  static bool attr_set = false;  // per instantiation; setting the attribute twice is harmless
-  if (!attr_set && smem > 48 * 1024) {
+  // per instantiation; static shared memory counts against the same 48 KB
+  // default, so the attribute is set whatever the dynamic size
+  static bool attr_set = false;
+  if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(ax_fiber_kernel<P, N1, KIND, EM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -620,7 +673,7 @@ cudaError_t launch_ax_em(const AxArgs &a) {
 
 template <class P, int N1, int KIND>
 cudaError_t launch_fiber_n(const AxArgs &a, double *G_out) {
-  using Sh = Shape<N1>;
+  using Sh = Shape<N1, 1, kFillWarps<P, N1, KIND>>;
   if (G_out) {
     const int64_t blocks = (a.E + Sh::EPB - 1) / Sh::EPB;
     if (blocks <= 0) return cudaSuccess;

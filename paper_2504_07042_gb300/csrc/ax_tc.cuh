@@ -36,7 +36,7 @@ enum Mode { kTF32 = 0, kBF16 = 1, kFP16 = 2 };
 template <int N1>
 struct TcShape {
   static constexpr int F = N1 * N1;                     // fibers per direction and element
-  static constexpr int EPB = (F >= 128) ? 1 : 128 / F;  // elements per CTA
+  static constexpr int EPB = fiber::pick_epb(F);        // elements per CTA
   static constexpr int GT = F * EPB;                    // geometry threads (one per t-fiber)
   static constexpr int threads = (GT + 31) / 32 * 32;   // whole warps for mma.sync
   static constexpr int warps = threads / 32;
@@ -268,8 +268,10 @@ cudaError_t launch_tc_kind(const AxArgs &a, const float *Dp) {
   const int64_t grid = a.grid > 0 && a.grid < nblk ? a.grid : nblk;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
   const size_t smem = (size_t)4 * Sh::EPB * Sh::ES * sizeof(float);
+  // per instantiation; static shared memory counts against the same 48 KB
+  // default, so the attribute is set whatever the dynamic size
   static bool attr_set = false;
-  if (!attr_set && smem > 48 * 1024) {
+  if (!attr_set) {
     cudaError_t e =
         cudaFuncSetAttribute(ax_tc_kernel<MODE, N1, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
