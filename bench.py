@@ -40,13 +40,23 @@ FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (meas
 
 # dram bytes per launch from committed ncu captures, valid while the kernel
 # sources hash to the recorded value (else reported as null).
-TRAFFIC = {}
+# DRAM traffic per launch of the headline kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 32^3-element case of
+# the same kernel (profiles/ax_dw_trilinear_n7_e32768_full.md), scaled by
+# elements to the 64x64x32 workload (traffic grows with the element count);
+# valid while the kernel's sources hash to "src".
+TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.590592e6 + 84.163584e6), "src": "6f23e95367de01eb"}}
+
+
+# the sources that define the headline kernel (double-word AxLocal, N = 7)
+KERNEL_SOURCES = ("ax_fiber.cuh", "dw.cuh", "inst_fiber.inc", "ax_dw_g1.cu", "tables.cuh", "ax_internal.h",
+                  "gll.cpp", "gll.h")
 
 
 def _src_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2504_07042_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -289,7 +299,7 @@ def run(args):
     value = whole_job_value(world, E * n3, ms)
     roof = _roofline(info, ms, clocks.get("sm_mhz"), hbm)
     src = _src_hash()
-    kname = "ax_dw_kernel<8,%d>" % info["kind"]
+    kname = "ax_fiber_kernel<DW, 8, %d, 1>" % info["kind"]
     traffic = TRAFFIC.get(kname)
     roof_line = {"bound": roof["bound"], "achieved": roof["achieved"], "peak": roof["peak"], "unit": roof["unit"],
                  "frac": roof["frac"], "traffic": traffic["bytes"] if traffic and traffic["src"] == src else None,

@@ -173,11 +173,13 @@ __host__ __device__ constexpr int pick_epb(int F) {
 }
 
 // FILL: pick_epb; otherwise the plain 128-thread rule.  Measured on GB300:
-// filling the warps pays for the recompute kinds in 8-byte arithmetic
-// (double-word, FP64) and for FP32 at N1 = 6; the stored kind and FP32 at
-// N1 = 10, 12 run faster with the smaller CTAs (more of them per SM).
+// filling the warps pays for the trilinear kinds in 8-byte arithmetic
+// (double-word, FP64) and for every recompute kind at N1 = 6; the stored
+// and parallelepiped kinds elsewhere, and FP32 at N1 = 10, 12, run faster
+// with the smaller CTAs (more of them per SM).
 template <class P, int N1, int KIND>
-constexpr bool kFillWarps = KIND != AX_GEOM_STORED && (sizeof(typename P::S) == 8 || N1 == 6);
+constexpr bool kFillWarps =
+    KIND != AX_GEOM_STORED && (N1 == 6 || (sizeof(typename P::S) == 8 && KIND != AX_GEOM_PARALLELEPIPED));
 
 template <int N1, int EM = 1, bool FILL = false>
 struct Shape {

@@ -36,7 +36,7 @@ enum Mode { kTF32 = 0, kBF16 = 1, kFP16 = 2 };
 template <int N1>
 struct TcShape {
   static constexpr int F = N1 * N1;                     // fibers per direction and element
-  static constexpr int EPB = fiber::pick_epb(F);        // elements per CTA
+  static constexpr int EPB = N1 == 6 ? fiber::pick_epb(F) : (F >= 128 ? 1 : 128 / F);  // elements per CTA
   static constexpr int GT = F * EPB;                    // geometry threads (one per t-fiber)
   static constexpr int threads = (GT + 31) / 32 * 32;   // whole warps for mma.sync
   static constexpr int warps = threads / 32;

@@ -6,6 +6,13 @@
 Builds the perturbed-box mesh (or the parallelepiped box with --mesh
 parallelepiped), sets up the context, runs `--launches` AxLocal calls on the
 current stream and prints the CUDA-event time of each.
+
+Other modes (same box options):
+  --pcg K            K Jacobi-PCG iterations (--mixed: one outer step of the
+                     mixed solver with K inner iterations)
+  --learned K        K flexible-PCG iterations with the learned preconditioner
+                     (untrained network; N = 7, double-word context)
+  --mlp M            `--launches` MLP forward passes on M rows (tcgen05 GEMMs)
 """
 from __future__ import annotations
 
@@ -27,9 +34,15 @@ def main():
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--pcg", type=int, default=0, help="instead: run this many Jacobi-PCG iterations on the box")
     ap.add_argument("--mixed", action="store_true", help="with --pcg: the mixed-precision solver (float32 inner)")
+    ap.add_argument("--learned", type=int, default=0, help="instead: this many learned flexible-PCG iterations")
+    ap.add_argument("--mlp", type=int, default=0, help="instead: MLP forward passes on this many rows")
     a = ap.parse_args()
     if a.pcg:
         return run_pcg(a)
+    if a.learned:
+        return run_learned(a)
+    if a.mlp:
+        return run_mlp(a)
     ex, ey, ez = a.box
     V = inputs.parallelepiped_vertices(ex, ey, ez) if a.mesh == "parallelepiped" else \
         inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
@@ -84,6 +97,59 @@ def run_pcg(a):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
     print(json.dumps({"E": op.E, "N": N, "n_global": ng, "result": list(res), "seconds": dt}))
+
+
+def run_learned(a):
+    """--learned K flexible-PCG iterations (rtol 0) on the box, N = 7, double-word."""
+    import time
+
+    import torch
+
+    from paper_2504_07042_gb300 import ax, inputs, learned
+
+    ex, ey, ez = a.box
+    N = 7
+    V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    gid, ng = inputs.box_global_ids(ex, ey, ez, N)
+    mask = inputs.box_boundary_mask(ex, ey, ez, N)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, "trilinear", "f64dw")
+    op.gs_setup(torch.from_numpy(gid).to(dev), ng, torch.from_numpy(mask).to(dev))
+    XYZ = learned.node_coords(op).cpu().numpy()
+    b = learned.rhs_from_f(op, torch.from_numpy(inputs.smooth_rhs(XYZ, 300)).to(dev), ng)
+    mlp = ax.AxMLP(seed=2)
+    x = torch.zeros(ng, dtype=torch.float64, device=dev)
+    ax.pcg_solve_learned(op, mlp, b, x, rtol=0.0, maxit=16, omega=0.5, check=False)  # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = ax.pcg_solve_learned(op, mlp, b, x.zero_(), rtol=0.0, maxit=a.learned, omega=0.5, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"E": op.E, "n_global": ng, "result": list(res), "seconds": time.perf_counter() - t}))
+
+
+def run_mlp(a):
+    """--launches forward passes of the MLP on --mlp rows of random bf16 inputs."""
+    import torch
+
+    from paper_2504_07042_gb300 import ax
+
+    dev = torch.device("cuda:0")
+    mlp = ax.AxMLP(seed=2)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    X = torch.rand((a.mlp, ax.AxMLP.IN_PAD), generator=g, device=dev).to(torch.bfloat16)
+    Y = torch.empty((a.mlp, ax.AxMLP.OUT), dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(a.launches):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        mlp.ax_mlp_forward(X, Y, s)
+        t1.record(s)
+        torch.cuda.synchronize()
+        times.append(t0.elapsed_time(t1))
+    flops = 2.0 * a.mlp * (ax.AxMLP.IN_PAD * 512 + 512 * 512 + 512 * 512)
+    print(json.dumps({"rows": a.mlp, "ms": times, "tflops": [flops / (t * 1e-3) / 1e12 for t in times]}))
 
 
 if __name__ == "__main__":
