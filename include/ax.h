@@ -93,7 +93,11 @@ ax_status ax_local(ax_ctx *c, const void *X, void *Y, void *stream);
 
 /* Same as ax_local with host buffers (pageable or pinned): copies X to the
  * device, runs ax_local, copies Y back and synchronises the stream.  Uses
- * library-owned device buffers allocated at the first call. */
+ * library-owned device buffers allocated at the first call.  The elements
+ * are processed in up to 16 chunks (at least 2048 elements each) on three
+ * library streams (copy in, AxLocal, copy out) ordered by events, so the
+ * transfers overlap the kernels (pinned host memory lets them run
+ * asynchronously); the call is ordered after prior work on `stream`. */
 ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *stream);
 
 /* ax_local_host for callers that cannot allocate device memory at call time

@@ -253,12 +253,57 @@ ax_status ax_local(ax_ctx *c, const void *X, void *Y, void *stream) {
   return AX_OK;
 }
 
+// Host-buffer pipeline of ax_local_host: the elements are cut into chunks;
+// chunk i's host-to-device copy, AxLocal and device-to-host copy run on three
+// streams ordered by events, so the copies of one chunk overlap the kernels
+// and the opposite copies of its neighbours.
+namespace {
+constexpr int kHostChunks = 16;
+struct HostPipe {
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};  // h2d, compute, d2h
+  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t in[kHostChunks] = {}, out[kHostChunks] = {};
+  cudaError_t create() {
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaStreamCreateWithFlags(&st[q], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    for (int q = 0; q < kHostChunks && e == cudaSuccess; ++q) {
+      e = cudaEventCreateWithFlags(&in[q], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out[q], cudaEventDisableTiming);
+    }
+    return e;
+  }
+};
+void delete_host_pipe(void *p) {
+  HostPipe *h = static_cast<HostPipe *>(p);
+  for (int q = 0; q < 3; ++q)
+    if (h->st[q]) cudaStreamDestroy(h->st[q]);
+  if (h->start) cudaEventDestroy(h->start);
+  if (h->done) cudaEventDestroy(h->done);
+  for (int q = 0; q < kHostChunks; ++q) {
+    if (h->in[q]) cudaEventDestroy(h->in[q]);
+    if (h->out[q]) cudaEventDestroy(h->out[q]);
+  }
+  delete h;
+}
+
+// geometry words of one element in the context's record
+size_t geo_words_per_element(const ax_ctx *c) {
+  switch (c->c.kind) {
+    case AX_GEOM_STORED: return (size_t)7 * c->c.n3;
+    case AX_GEOM_PARALLELEPIPED: return ax::kParWords;
+    default: return ax::kVertexWords;
+  }
+}
+}  // namespace
+
 ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *stream) {
   if (!c) return fail(nullptr, AX_EINVAL, "ax_local_host: context is NULL");
   if (c->c.E == 0) return AX_OK;
   if (!X_host || !Y_host) return fail(c, AX_EINVAL, "ax_local_host: X or Y is NULL");
   if (!same_device(c)) return fail(c, AX_EINVAL, "ax_local_host: current device differs from the context's");
-  const size_t bytes = (size_t)c->c.E * c->c.n3 * io_word(c->c.prec);
+  const size_t word = io_word(c->c.prec), bytes = (size_t)c->c.E * c->c.n3 * word;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   if (c->c.hbytes < bytes) {
@@ -271,9 +316,45 @@ ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *strea
     if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host: staging allocation");
     c->c.hbytes = bytes;
   }
-  e = cudaMemcpyAsync(c->c.hx, X_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = run_ax(c, make_args(c, c->c.hx, c->c.hy, stream));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(Y_host, c->c.hy, bytes, cudaMemcpyDeviceToHost, s);
+  HostPipe *hp = static_cast<HostPipe *>(c->c.ws[ax::Ctx::kWsHost]);
+  if (!hp) {
+    hp = new (std::nothrow) HostPipe;
+    if (!hp) return fail(c, AX_ENOMEM, "ax_local_host: host allocation failed");
+    e = hp->create();
+    if (e != cudaSuccess) {
+      delete_host_pipe(hp);
+      return cuda_fail(c, e, "ax_local_host: streams");
+    }
+    c->c.ws[ax::Ctx::kWsHost] = hp;
+    c->c.ws_del[ax::Ctx::kWsHost] = delete_host_pipe;
+  }
+  // chunks of at least 2048 elements (small problems: one chunk)
+  int64_t per = (c->c.E + kHostChunks - 1) / kHostChunks;
+  if (per < 2048) per = 2048;
+  const int nch = (int)((c->c.E + per - 1) / per);
+  const size_t gw = storage_word(c->c.prec), gpe = geo_words_per_element(c), n3 = (size_t)c->c.n3;
+  e = cudaEventRecord(hp->start, s);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(hp->st[q], hp->start, 0);
+  for (int i = 0; i < nch && e == cudaSuccess; ++i) {
+    const int64_t e0 = i * per, ne = (c->c.E - e0) < per ? (c->c.E - e0) : per;
+    const size_t off = (size_t)e0 * n3 * word, len = (size_t)ne * n3 * word;
+    e = cudaMemcpyAsync((char *)c->c.hx + off, (const char *)X_host + off, len, cudaMemcpyHostToDevice, hp->st[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(hp->in[i], hp->st[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->st[1], hp->in[i], 0);
+    if (e == cudaSuccess) {
+      ax::AxArgs a = make_args(c, (const char *)c->c.hx + off, (char *)c->c.hy + off, hp->st[1]);
+      a.E = ne;
+      a.geo = (const char *)c->c.geo + (size_t)e0 * gpe * gw;
+      if (c->c.lam) a.lam = (const char *)c->c.lam + (size_t)e0 * n3 * gw;
+      e = run_ax(c, a);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(hp->out[i], hp->st[1]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->st[2], hp->out[i], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char *)Y_host + off, (const char *)c->c.hy + off, len, cudaMemcpyDeviceToHost, hp->st[2]);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(hp->done, hp->st[2]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hp->done, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host");
   return AX_OK;

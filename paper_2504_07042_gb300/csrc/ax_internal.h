@@ -60,9 +60,9 @@ struct Ctx {
   float *diag32 = nullptr;
   // solver workspaces kept between calls (work vectors, streams, captured
   // graphs), each with its deleter; freed by gs_setup and ax_destroy
-  enum { kWsCg64 = 0, kWsCg32 = 1, kWsMixed = 2, kWsLearn = 3, kNumWs = 4 };
-  void *ws[kNumWs] = {nullptr, nullptr, nullptr, nullptr};
-  void (*ws_del[kNumWs])(void *) = {nullptr, nullptr, nullptr, nullptr};
+  enum { kWsCg64 = 0, kWsCg32 = 1, kWsMixed = 2, kWsLearn = 3, kWsHost = 4, kNumWs = 5 };
+  void *ws[kNumWs] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  void (*ws_del[kNumWs])(void *) = {nullptr, nullptr, nullptr, nullptr, nullptr};
   void free_ws() {
     for (int q = 0; q < kNumWs; ++q) {
       if (ws[q] && ws_del[q]) ws_del[q](ws[q]);

@@ -155,6 +155,28 @@ def test_host_entry_point_matches_device(ax):
     np.testing.assert_array_equal(Yh, Yd.cpu().numpy())
 
 
+@pytest.mark.parametrize("kind,prec", [("stored", "f64dw"), ("partial", "fp32"), ("parallelepiped", "fp64"),
+                                       ("trilinear", "tf32")])
+def test_host_pipeline_chunks_match_device(ax, kind, prec):
+    # 20x16x16 = 5120 elements: three chunks of the host pipeline, the last one ragged;
+    # every chunk must find its own slice of the geometry record
+    N = 3
+    V = _mesh(kind, 20, 16, 16)
+    X = inputs.element_vectors(V.shape[0], N, seed=2)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, prec)
+    Xd = torch.from_numpy(X).to(dev, op.dtype)
+    Yd = torch.empty_like(Xd)
+    op.ax_local(Xd, Yd)
+    Xh = Xd.cpu().pin_memory()
+    Yh = torch.empty_like(Xh).pin_memory()
+    op.ax_local_host(Xh, Yh)
+    assert torch.equal(Yh, Yd.cpu())
+    Yp = np.empty(X.shape, dtype=Xh.numpy().dtype)  # pageable host memory too
+    op.ax_local_host(Xh.numpy(), Yp)
+    np.testing.assert_array_equal(Yp, Yd.cpu().numpy())
+
+
 def test_node_coords(ax, orc):
     N = 4
     V = _mesh("trilinear", 3, 2, 2)
