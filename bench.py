@@ -403,7 +403,8 @@ def run_batch(ax, torch, dev):
     """64 perturbed-box meshes, E log-uniform on [64, 4096] (near-cubic boxes),
     N uniform on {3,5,7,9}, FP32, trilinear recompute: batched AxLocal (one
     launch per order) and batched Jacobi-PCG (one CUDA-graph launch per CG
-    iteration) against the per-mesh paths (one launch per mesh per step)."""
+    iteration) against the per-mesh paths (one launch per mesh per step);
+    then the batched paths with TF32 tensor-core contractions."""
     from paper_2504_07042_gb300 import inputs
     spec = inputs.batch_meshes()
     meshes = []
@@ -452,6 +453,21 @@ def run_batch(ax, torch, dev):
     out["pcg_speedup_graph_over_per_mesh"] = out["pcg_per_mesh"]["seconds"] / out["pcg_graph"]["seconds"]
     for op in per:
         op.ax_destroy()
+    bt.ax_batch_destroy()
+    # the same batch with TF32 tensor-core contractions (FP32 accumulation)
+    bt = ax.AxBatch(meshes, "trilinear", "tf32")
+    bt.ax_batch_tune()
+    t_tc = _time_launches(torch, lambda: bt.ax_batch_local(X, Y, stream), 10, 3, stream)
+    x = torch.zeros_like(bvec)
+    bt.ax_batch_pcg(bvec, x, rtol=1e-5, maxit=20000, graph=1)  # warm-up
+    x.zero_()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    it, rr, st = bt.ax_batch_pcg(bvec, x, rtol=1e-5, maxit=20000, graph=1)
+    torch.cuda.synchronize()
+    out["tf32"] = {"axlocal_batched_ms": t_tc, "axlocal_batched_gdofs": bt.n_local / (t_tc * 1e-3) / 1e9,
+                   "pcg_graph": {"seconds": time.perf_counter() - t, "status": st, "max_iterations": max(it),
+                                 "total_iterations": sum(it), "max_relres": max(rr)}}
     bt.ax_batch_destroy()
     return out
 

@@ -38,7 +38,7 @@ def _dev(meshes):
             for V, N, g, ng, m in meshes]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "f64dw"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "f64dw", "tf32", "bf16"])
 def test_batch_local_equals_per_mesh(ax, prec):
     meshes = _meshes()
     bt = ax.AxBatch(_dev(meshes), "trilinear", prec)
