@@ -232,6 +232,15 @@ def cpu_oracle_rate(seconds=10.0, N=HEADLINE_N):
             "%d pass(es) over the first %d of %d elements (%.1f s)" % (reps, m, V.shape[0], dt))
 
 
+def headline_config(world):
+    """The workload the bench line measures (both arms report it)."""
+    return {"workload": "order sweep at N=7: perturbed trilinear box 64x64x32 = 131072 elements, "
+                        "67.1M local DOFs, X~U(-1,1) float64",
+            "kind": HEADLINE_KIND, "precision": "float64 in/out, double-word FP32-pair arithmetic",
+            "l2": "inputs larger than L2 (1.07 GB per step); no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -255,10 +264,10 @@ def run_reference(args):
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "order-7 sweep mesh 64x64x32 perturbed trilinear, %d-element sample per step" % m,
-                       "kind": HEADLINE_KIND},
+            "config": headline_config(world),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "%d elements per step of the 131072-element mesh" % m},
+                             "sample": "FP64 CPU oracle on %d elements per step (a bounded sample of the "
+                                       "131072-element workload), float64 arithmetic" % m},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -337,11 +346,7 @@ def run(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64dw", "data": "synthetic",
-            "config": {"workload": "order sweep at N=7: perturbed trilinear box 64x64x32 = 131072 elements, "
-                                   "67.1M local DOFs, X~U(-1,1) float64",
-                       "kind": HEADLINE_KIND, "precision": "float64 in/out, double-word FP32-pair arithmetic",
-                       "l2": "inputs larger than L2 (1.07 GB per step); no flush",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": headline_config(world),
             "roofline": roof_line, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
     if rank == 0:
         rate, cores, sample = cpu_oracle_rate()
