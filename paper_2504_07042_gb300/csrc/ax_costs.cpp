@@ -22,33 +22,22 @@ double pipe_ops_per_node(int N1, int kind, int prec) {
   ops += 3.0 * (3.0 * mac + fin);        // (r, s, t) = G (x0, x1, x2)
   ops += 2.0 * add;                      // Y accumulation of passes 3 and 4
   // trilinear geometry (Algorithm 2 with K = J^T J and det J as polynomials in t):
-  // per thread (i,j): edges, E0/E1/F0/F1/Jc2, 19 dot products and 6 two-term
-  // determinants for the coefficients, amortised over the N1 nodes of its fiber
+  // per thread (i,j), from the record's monomial coefficients: E0/E1/F0/F1
+  // (12 multiply-adds), J2 (3 dot products of 3 terms plus C), the 15 dot
+  // products of the K coefficients and, for det J, 6 two-term determinants
+  // and 4 dot products, amortised over the N1 nodes of its fiber
   const double dot3 = 3.0 * mac + fin, det2 = 2.0 * mac + fin;
-  const double prologue = 36.0 * add + 12.0 * (2.0 * add + mul + fma) + 3.0 * (4.0 * mac + fin) + 12.0 * mul;
-  const double coeffs = 13.0 * dot3 + 3.0 * add, det_coeffs = 6.0 * det2 + 4.0 * dot3 + add;
+  const double cols = 12.0 * (mul + add) + 3.0 * (3.0 * mac + fin + add) + mul;
+  const double coeffs = 15.0 * dot3 + 3.0 * add, det_coeffs = 6.0 * det2 + 4.0 * dot3 + add;
   const double quad = 2.0 * fma, lin = fma;
   const double knode = 3.0 * quad + 2.0 * lin, adj = 6.0 * det2, scale = 3.0 * mul;
-  // FP64 shares the element terms (E0/E1 per s-point, F0/F1 per r-point, the
-  // t-edges and K00/K11 coefficients) among the element's threads: 2 N1 + 1
-  // producers per element instead of every thread
-  const bool share = (prec == AX_FP64);
-  const double n3 = (double)N1 * N1 * N1;
-  const double j2 = 3.0 * (4.0 * mac + fin) + 12.0 * mul;
-  const double own = j2 + 4.0 * dot3 + add + 4.0 * dot3 + dot3;  // J2, K01, K02, K12, K22
-  const double item = 12.0 * add + 6.0 * (2.0 * add + mul + fma) + 3.0 * dot3 + add + 4.0 * add;
-  const double shared_terms = (2.0 * N1 * item + 12.0 * add) / n3;
   switch (kind) {
     case AX_GEOM_STORED: break;
     case AX_GEOM_PARALLELEPIPED: ops += mul + 3.0 * mul; break;
     case AX_GEOM_TRILINEAR:
-      ops += knode + quad + adj + mul + div + scale;
-      ops += share ? (own + det_coeffs) / N1 + shared_terms : (prologue + coeffs + det_coeffs) / N1;
+      ops += knode + quad + adj + mul + div + scale + (cols + coeffs + det_coeffs) / N1;
       break;
-    case AX_GEOM_TRILINEAR_PARTIAL:
-      ops += knode + adj + scale;
-      ops += share ? own / N1 + shared_terms : (prologue + coeffs) / N1;
-      break;
+    case AX_GEOM_TRILINEAR_PARTIAL: ops += knode + adj + scale + (cols + coeffs) / N1; break;
   }
   return ops;
 }

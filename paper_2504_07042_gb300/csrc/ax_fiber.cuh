@@ -44,10 +44,6 @@ struct Native {
   using IO = T;  // X, Y in HBM
   static constexpr bool kRoll = false;  // short code: unroll the phase and k loops
   static constexpr int kTiles = sizeof(T) == 4 ? 2 : 1;  // tile variants the autotuner may pick
-  // per-element geometry terms computed once per element (Geometry::element_terms):
-  // pays where the binding pipe is shared by all warps (FP64); on the FP32
-  // pipe the few threads that compute them become the element's critical path
-  static constexpr bool kShareTerms = sizeof(T) == 8;
   __device__ static __forceinline__ V ld(const S *p) { return *p; }
   __device__ static __forceinline__ S st(V v) { return v; }
   __device__ static __forceinline__ V cst(const C *p) { return *p; }
@@ -77,7 +73,6 @@ struct DW {
   using IO = double;
   static constexpr bool kRoll = true;  // long code: keep the phase and k loops rolled (instruction cache)
   static constexpr int kTiles = 1;
-  static constexpr bool kShareTerms = false;
   __device__ static __forceinline__ V ld(const S *p) { return dw::from_float2(*p); }
   __device__ static __forceinline__ S st(V v) { return make_float2(v.hi, v.lo); }
   __device__ static __forceinline__ V cst(const C *p) { return dw::from_float2(*p); }
@@ -94,8 +89,6 @@ struct DW {
   __device__ static __forceinline__ V neg(V a) { return dw::neg(a); }
 };
 
-template <class P, int KIND>
-constexpr bool kSharedTerms = P::kShareTerms && (KIND == AX_GEOM_TRILINEAR || KIND == AX_GEOM_TRILINEAR_PARTIAL);
 
 template <class P>
 __device__ __forceinline__ typename P::V dot3(const typename P::V a[3], const typename P::V b[3]) {
@@ -195,7 +188,9 @@ struct Shape {
 // ---------------------------------------------------------------------------
 // geometry (getFactors of Algorithm 4) in policy arithmetic
 //
-// Trilinear (Algorithm 2, true Jacobian): thread (i,j) holds the columns
+// Trilinear (Algorithm 2, true Jacobian): the element's record holds the
+// map's monomial coefficients (A..G of x = x0 + Ar + Bs + Ct + Drs + Ert +
+// Fst + Grst, Eq. 8), from which thread (i,j) forms the columns
 //   J0(t) = E0 + t E1  (E0, E1 depend on s = xi_j),
 //   J1(t) = F0 + t F1  (F0, F1 depend on r = xi_i),   J2 = Jc2(r, s),
 // so along its k-fiber (t = xi_k) every entry of K = J^T J is a polynomial
@@ -213,56 +208,8 @@ struct Geometry {
   V h[7];
   const S *gl = nullptr;
 
-  // Terms of the trilinear geometry shared by all threads of an element,
-  // computed once per element by 2 N1 + 1 threads (w) into shared memory se:
-  //   [0, 12)               the four t-edges c00 c10 c01 c11 (3 coordinates each)
-  //   [12 + 6 j, ...)       E0[3], E1[3] at s = xi_j          (w = j < N1)
-  //   [12 + 6 N1 + 6 i, ..) F0[3], F1[3] at r = xi_i          (w = N1 + i)
-  //   [12 + 12 N1 + 3 j, ..) t-coefficients of K00 at s = xi_j
-  //   [12 + 15 N1 + 3 i, ..) t-coefficients of K11 at r = xi_i  (w = 2 N1: the t-edges)
-  static constexpr int kTerms = 12 + 18 * N1;
-  __device__ static __forceinline__ void element_terms(const S *sv, const typename P::C *xg, int w, S *se) {
-    auto Vx = [&](int v, int c) { return P::ld(sv + 3 * v + c); };
-    const V one = P::lit(1.0), eighth = P::lit(0.125);
-    if (w < 2 * N1) {
-      const bool isE = w < N1;
-      const int pidx = isE ? w : w - N1;
-      const V xi = P::cst(xg + pidx);
-      const V u0 = P::mul(P::sub(one, xi), eighth), u1 = P::mul(P::add(one, xi), eighth);
-      V A0[3], A1[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        // E: edges along r (a_bc) weighted in s; F: edges along s (b_ac) weighted in r
-        const V e00 = isE ? P::sub(Vx(1, c), Vx(0, c)) : P::sub(Vx(2, c), Vx(0, c));
-        const V e10 = isE ? P::sub(Vx(3, c), Vx(2, c)) : P::sub(Vx(3, c), Vx(1, c));
-        const V e01 = isE ? P::sub(Vx(5, c), Vx(4, c)) : P::sub(Vx(6, c), Vx(4, c));
-        const V e11 = isE ? P::sub(Vx(7, c), Vx(6, c)) : P::sub(Vx(7, c), Vx(5, c));
-        A0[c] = P::add(P::mul(u0, P::add(e00, e01)), P::mul(u1, P::add(e10, e11)));
-        A1[c] = P::add(P::mul(u0, P::sub(e01, e00)), P::mul(u1, P::sub(e11, e10)));
-      }
-      S *dst = se + 12 + (isE ? 6 * pidx : 6 * N1 + 6 * pidx);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        dst[c] = P::st(A0[c]);
-        dst[3 + c] = P::st(A1[c]);
-      }
-      S *kq = se + 12 + 12 * N1 + (isE ? 3 * pidx : 3 * N1 + 3 * pidx);
-      kq[0] = P::st(dot3<P>(A0, A0));
-      kq[1] = P::st(P::add(dot3<P>(A0, A1), dot3<P>(A0, A1)));
-      kq[2] = P::st(dot3<P>(A1, A1));
-    } else if (w == 2 * N1) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        se[c] = P::st(P::sub(Vx(4, c), Vx(0, c)));
-        se[3 + c] = P::st(P::sub(Vx(5, c), Vx(1, c)));
-        se[6 + c] = P::st(P::sub(Vx(6, c), Vx(2, c)));
-        se[9 + c] = P::st(P::sub(Vx(7, c), Vx(3, c)));
-      }
-    }
-  }
-
-  __device__ __forceinline__ void prologue(const S *sv, const S *se, const typename P::C *xg,
-                                           const typename P::C *wg, int i, int j, const S *G_e, const S *lam_e) {
+  __device__ __forceinline__ void prologue(const S *sv, const typename P::C *xg, const typename P::C *wg, int i,
+                                           int j, const S *G_e, const S *lam_e) {
     wij = P::mul(P::cst(wg + i), P::cst(wg + j));
     if constexpr (KIND == AX_GEOM_STORED) {
       gl = G_e;
@@ -270,59 +217,26 @@ struct Geometry {
 #pragma unroll
       for (int q = 0; q < 7; ++q) h[q] = P::ld(sv + q);
     } else {
+      // columns of J from the monomial coefficients of the map (Eq. 8):
+      // J0 = E0 + t E1, E0 = A + D s, E1 = E + G s;  J1 = F0 + t F1, F0 = B + D r,
+      // F1 = F + G r;  J2 = C + E r + F s + G rs   (r = xi_i, s = xi_j)
       V E0[3], E1[3], F0[3], F1[3], J2[3];
-      const V r = P::cst(xg + i), s = P::cst(xg + j);
-      const V one = P::lit(1.0), eighth = P::lit(0.125);
-      const V sm = P::sub(one, s), sp = P::add(one, s);
-      const V v0 = P::mul(P::sub(one, r), eighth), v1 = P::mul(P::add(one, r), eighth);
-      const V w00 = P::mul(v0, sm), w10 = P::mul(v1, sm), w01 = P::mul(v0, sp), w11 = P::mul(v1, sp);
-      if constexpr (kSharedTerms<P, KIND>) {
-        const S *ej = se + 12 + 6 * j, *fi = se + 12 + 6 * N1 + 6 * i;
+      const V r = P::cst(xg + i), s = P::cst(xg + j), rs = P::mul(r, s);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          E0[c] = P::ld(ej + c);
-          E1[c] = P::ld(ej + 3 + c);
-          F0[c] = P::ld(fi + c);
-          F1[c] = P::ld(fi + 3 + c);
-          typename P::A q = P::zero();
-          P::mac(q, w00, P::ld(se + c));
-          P::mac(q, w10, P::ld(se + 3 + c));
-          P::mac(q, w01, P::ld(se + 6 + c));
-          P::mac(q, w11, P::ld(se + 9 + c));
-          J2[c] = P::fin(q);
-        }
-        const S *kj = se + 12 + 12 * N1 + 3 * j, *ki = se + 12 + 15 * N1 + 3 * i;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          k00[q] = P::ld(kj + q);
-          k11[q] = P::ld(ki + q);
-        }
-      } else {
-        const V u0 = P::mul(sm, eighth), u1 = P::mul(sp, eighth);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          auto Vx = [&](int v) { return P::ld(sv + 3 * v + c); };
-          // edges along r (a_bc), s (b_ac), t (c_ab) of the trilinear map (Eq. 8)
-          const V a00 = P::sub(Vx(1), Vx(0)), a10 = P::sub(Vx(3), Vx(2));
-          const V a01 = P::sub(Vx(5), Vx(4)), a11 = P::sub(Vx(7), Vx(6));
-          const V b00 = P::sub(Vx(2), Vx(0)), b10 = P::sub(Vx(3), Vx(1));
-          const V b01 = P::sub(Vx(6), Vx(4)), b11 = P::sub(Vx(7), Vx(5));
-          const V c00 = P::sub(Vx(4), Vx(0)), c10 = P::sub(Vx(5), Vx(1));
-          const V c01 = P::sub(Vx(6), Vx(2)), c11 = P::sub(Vx(7), Vx(3));
-          E0[c] = P::add(P::mul(u0, P::add(a00, a01)), P::mul(u1, P::add(a10, a11)));
-          E1[c] = P::add(P::mul(u0, P::sub(a01, a00)), P::mul(u1, P::sub(a11, a10)));
-          F0[c] = P::add(P::mul(v0, P::add(b00, b01)), P::mul(v1, P::add(b10, b11)));
-          F1[c] = P::add(P::mul(v0, P::sub(b01, b00)), P::mul(v1, P::sub(b11, b10)));
-          typename P::A q = P::zero();
-          P::mac(q, w00, c00);
-          P::mac(q, w10, c10);
-          P::mac(q, w01, c01);
-          P::mac(q, w11, c11);
-          J2[c] = P::fin(q);
-        }
-        k00[0] = dot3<P>(E0, E0); k00[1] = P::add(dot3<P>(E0, E1), dot3<P>(E0, E1)); k00[2] = dot3<P>(E1, E1);
-        k11[0] = dot3<P>(F0, F0); k11[1] = P::add(dot3<P>(F0, F1), dot3<P>(F0, F1)); k11[2] = dot3<P>(F1, F1);
+      for (int c = 0; c < 3; ++c) {
+        auto M = [&](int m) { return P::ld(sv + 3 * m + c); };  // A B C D E F G = 0..6
+        E0[c] = P::add(M(0), P::mul(M(3), s));
+        E1[c] = P::add(M(4), P::mul(M(6), s));
+        F0[c] = P::add(M(1), P::mul(M(3), r));
+        F1[c] = P::add(M(5), P::mul(M(6), r));
+        typename P::A q = P::zero();
+        P::mac(q, M(4), r);
+        P::mac(q, M(5), s);
+        P::mac(q, M(6), rs);
+        J2[c] = P::add(M(2), P::fin(q));
       }
+      k00[0] = dot3<P>(E0, E0); k00[1] = P::add(dot3<P>(E0, E1), dot3<P>(E0, E1)); k00[2] = dot3<P>(E1, E1);
+      k11[0] = dot3<P>(F0, F0); k11[1] = P::add(dot3<P>(F0, F1), dot3<P>(F0, F1)); k11[2] = dot3<P>(F1, F1);
       // K = J^T J as polynomials in t
       k01[0] = dot3<P>(E0, F0); k01[1] = P::add(dot3<P>(E0, F1), dot3<P>(E1, F0)); k01[2] = dot3<P>(E1, F1);
       k02[0] = dot3<P>(E0, J2); k02[1] = dot3<P>(E1, J2);
@@ -444,8 +358,6 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   S *b0 = xs + EPB * ES;       // x0, later r
   S *b1 = b0 + EPB * ES;       // x1, later s
   __shared__ S sgeo[EPB][GW > 0 ? GW : 1];
-  constexpr int NT = kSharedTerms<P, KIND> ? Geometry<P, N1, KIND>::kTerms : 1;
-  __shared__ S sterm[EPB][NT];
 
   const int tid = threadIdx.x;
   const int z = tid / Sh::F, q = tid % Sh::F;
@@ -476,11 +388,6 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
   }
   __syncthreads();
-  if constexpr (kSharedTerms<P, KIND>) {
-    // per-element geometry terms (read after the barrier that ends the forward passes)
-    if (live)
-      for (int w = q; w < 2 * N1 + 1; w += Sh::F) Geometry<P, N1, KIND>::element_terms(sgeo[z], cx, w, sterm[z]);
-  }
 
   S *x_e = xs + z * ES, *r_e = b0 + z * ES, *s_e = b1 + z * ES;
   // Six fiber products in two rolled phase loops (one code copy of the fiber
@@ -531,7 +438,7 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     // thread (i, j) = (qa, qb): geometry and G x along its own t-fiber
     const int i = qa, j = qb;
     Geometry<P, N1, KIND> gm;
-    gm.prologue(sgeo[z], sterm[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+    gm.prologue(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
                 (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
     auto node = [&](int k) {
       const int sidx = ft + k * str_t;
@@ -570,7 +477,7 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     {
       const int i = qa, j = qb;
       Geometry<P, N1, KIND> gm;
-      gm.prologue(sgeo[z], sterm[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+      gm.prologue(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
                   (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
@@ -618,8 +525,6 @@ __global__ void __launch_bounds__(Shape<N1, 1, kFillWarps<P, N1, KIND>>::threads
   constexpr int n3 = Sh::n3, EPB = Sh::EPB;
   constexpr int GW = GeoWords<KIND>::value;
   __shared__ S sgeo[EPB][GW > 0 ? GW : 1];
-  constexpr int NT = kSharedTerms<P, KIND> ? Geometry<P, N1, KIND>::kTerms : 1;
-  __shared__ S sterm[EPB][NT];
   const int tid = threadIdx.x;
   const int z = tid / Sh::F, q = tid % Sh::F;
   const int i = q % N1, j = q / N1;
@@ -632,14 +537,9 @@ __global__ void __launch_bounds__(Shape<N1, 1, kFillWarps<P, N1, KIND>>::threads
     for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
   }
   __syncthreads();
-  if constexpr (kSharedTerms<P, KIND>) {
-    if (z < nel)
-      for (int w = q; w < 2 * N1 + 1; w += Sh::F) Geometry<P, N1, KIND>::element_terms(sgeo[z], cx, w, sterm[z]);
-    __syncthreads();
-  }
   if (z >= nel) return;
   Geometry<P, N1, KIND> gm;
-  gm.prologue(sgeo[z], sterm[z], cx, cw, i, j, KIND == AX_GEOM_STORED ? geo + e * 7 * n3 : nullptr,
+  gm.prologue(sgeo[z], cx, cw, i, j, KIND == AX_GEOM_STORED ? geo + e * 7 * n3 : nullptr,
               KIND == AX_GEOM_TRILINEAR_PARTIAL ? lam + e * n3 : nullptr);
   for (int k = 0; k < N1; ++k) {
     const int l = i + j * N1 + k * N1 * N1;

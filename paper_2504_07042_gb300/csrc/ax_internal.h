@@ -13,7 +13,7 @@
 namespace ax {
 
 // Per-element geometry record sizes (words of the storage type).
-constexpr int kVertexWords = 24;  // 8 vertices x 3, relative to vertex 0 (row 0 is zero)
+constexpr int kVertexWords = 24;  // trilinear record: 7 monomial coefficients x 3 (Eq. 8) + 3 pad
 constexpr int kParWords = 8;      // h0..h6 of Algorithm 3 + one pad word
 
 // Device tables for one polynomial order, uploaded once per device by each

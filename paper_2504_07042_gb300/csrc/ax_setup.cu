@@ -132,12 +132,33 @@ __global__ void stored_factors_kernel(int64_t E, int N1, const double *__restric
 }
 
 // Vertices relative to vertex 0 (24 words per element; row 0 is zero).
-__global__ void relative_vertices_kernel(int64_t E, const double *__restrict__ V, void *out, int fmt, int *flags) {
+// TRILINEAR record: the trilinear map of Eq. 8 written in the monomial basis,
+//   x(r,s,t) = x0 + A r + B s + C t + D rs + E rt + F st + G rst,
+// each coefficient (1/8) sum_v sigma(v) (V_v - V_0) with the sign pattern of
+// its monomial (sigma = +-1 from the vertex's corner, v = a + 2b + 4c); the
+// vertex-0 offset cancels in every sign sum, and subtracting it first keeps
+// the sums free of cancellation far from the origin.  Words: A B C D E F G
+// (3 coordinates each) and 3 zero pads.  Then the Jacobian's columns are
+//   J0 = (A + D s) + t (E + G s),  J1 = (B + D r) + t (F + G r),
+//   J2 = C + E r + F s + G r s.
+__global__ void trilinear_coeffs_kernel(int64_t E, const double *__restrict__ V, void *out, int fmt, int *flags) {
   const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= E * 24) return;
   const int64_t e = gidx / 24;
-  const int q = (int)(gidx % 24), c = q % 3;
-  store(out, gidx, V[24 * e + q] - V[24 * e + c], fmt, flags);
+  const int q = (int)(gidx % 24), m = q / 3, c = q % 3;
+  double acc = 0.0;
+  if (m < 7) {
+    // monomials r, s, t, rs, rt, st, rst: which of (a, b, c) enter the sign
+    const int use[7] = {1, 2, 4, 3, 5, 6, 7};
+    for (int v = 0; v < 8; ++v) {
+      int sgn = 1;
+      for (int d = 0; d < 3; ++d)
+        if ((use[m] >> d) & 1) sgn *= ((v >> d) & 1) ? 1 : -1;
+      acc += sgn * (V[24 * e + 3 * v + c] - V[24 * e + c]);
+    }
+    acc *= 0.125;
+  }
+  store(out, gidx, acc, fmt, flags);
 }
 
 // PARALLELEPIPED: J = [v1-v0, v2-v0, v4-v0] / 2 (columns) is constant;
@@ -267,10 +288,10 @@ cudaError_t setup_geometry(const Ctx &c, const double *V, void *geo, void *lam, 
       break;
     case AX_GEOM_TRILINEAR_PARTIAL:
       partial_lam_kernel<<<grid_for(nodes, B), B, 0, s>>>(c.E, c.N1, V, lam, fmt, flags);
-      relative_vertices_kernel<<<grid_for(c.E * 24, B), B, 0, s>>>(c.E, V, geo, fmt, flags);
+      trilinear_coeffs_kernel<<<grid_for(c.E * 24, B), B, 0, s>>>(c.E, V, geo, fmt, flags);
       break;
     case AX_GEOM_TRILINEAR:
-      relative_vertices_kernel<<<grid_for(c.E * 24, B), B, 0, s>>>(c.E, V, geo, fmt, flags);
+      trilinear_coeffs_kernel<<<grid_for(c.E * 24, B), B, 0, s>>>(c.E, V, geo, fmt, flags);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -174,8 +174,6 @@ __global__ void __launch_bounds__(TcShape<N1>::threads)
   float *xs = (float *)smem_raw;  // [EPB][ES] x
   float *bb = xs + EPB * ES;      // b0, b1, b2: [3][EPB][ES]
   __shared__ float sgeo[EPB][GW > 0 ? GW : 1];
-  constexpr int NTM = fiber::kSharedTerms<P, KIND> ? fiber::Geometry<P, N1, KIND>::kTerms : 1;
-  __shared__ float sterm[EPB][NTM];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float *cw = fiber::c_w + tab_off_v(N1);
@@ -204,12 +202,6 @@ __global__ void __launch_bounds__(TcShape<N1>::threads)
       for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
     }
     __syncthreads();
-    if constexpr (fiber::kSharedTerms<P, KIND>) {
-      // per-element geometry terms (read after the barrier that ends the forward passes)
-      if (tid < Sh::GT && tid / Sh::F < nel)
-        for (int w = tid % Sh::F; w < 2 * N1 + 1; w += Sh::F)
-          fiber::Geometry<P, N1, KIND>::element_terms(sgeo[tid / Sh::F], cx, w, sterm[tid / Sh::F]);
-    }
     // forward: x0, x1, x2 = D_r x, D_s x, D_t x
     for (int d = 0; d < 3; ++d)
       for (int u = warp; u < Sh::UNITS; u += Sh::warps) {
@@ -224,7 +216,7 @@ __global__ void __launch_bounds__(TcShape<N1>::threads)
       const int64_t e = e0 + z;
       float *r_e = bb + z * ES, *s_e = bb + (EPB + z) * ES, *t_e = bb + (2 * EPB + z) * ES;
       fiber::Geometry<P, N1, KIND> gm;
-      gm.prologue(sgeo[z], sterm[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+      gm.prologue(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
                   (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
