@@ -43,6 +43,7 @@ struct Native {
   using C = T;   // constant-table word
   using IO = T;  // X, Y in HBM
   static constexpr bool kRoll = false;  // short code: unroll the phase and k loops
+  static constexpr int kTargetWarpsPerSM = 0;  // no cap
   static constexpr int kTiles = sizeof(T) == 4 ? 2 : 1;  // tile variants the autotuner may pick
   __device__ static __forceinline__ V ld(const S *p) { return *p; }
   __device__ static __forceinline__ S st(V v) { return v; }
@@ -73,6 +74,12 @@ struct DW {
   using IO = double;
   static constexpr bool kRoll = true;  // long code: keep the phase and k loops rolled (instruction cache)
   static constexpr int kTiles = 1;
+  // Resident warps per SM the launcher aims at for the trilinear kinds at
+  // N1 = 8 (by padding the dynamic shared memory): more warps thrash the
+  // instruction cache with this long code (measured on GB300: 4 CTAs of 4
+  // warps 8% faster than the 7 that registers allow; at other orders and for
+  // the stored kind the cap measured slower, so it is not applied there).
+  static constexpr int kTargetWarpsPerSM = 16;
   __device__ static __forceinline__ V ld(const S *p) { return dw::from_float2(*p); }
   __device__ static __forceinline__ S st(V v) { return make_float2(v.hi, v.lo); }
   __device__ static __forceinline__ V cst(const C *p) { return dw::from_float2(*p); }
@@ -557,7 +564,22 @@ cudaError_t launch_ax_em(const AxArgs &a) {
   if (nblk <= 0) return cudaSuccess;
   int64_t grid = a.grid > 0 && a.grid < nblk ? a.grid : nblk;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)3 * Sh::EPB * Sh::ES * sizeof(typename P::S);
+  size_t smem = (size_t)3 * Sh::EPB * Sh::ES * sizeof(typename P::S);
+  if constexpr (P::kTargetWarpsPerSM > 0 && N1 == 8 &&
+                (KIND == AX_GEOM_TRILINEAR || KIND == AX_GEOM_TRILINEAR_PARTIAL)) {
+    // cap the resident CTAs by their shared memory (the kernel uses only its share)
+    static int sm_smem = 0;
+    if (!sm_smem) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
+    const int warps = (Sh::threads + 31) / 32;
+    int ctas = (P::kTargetWarpsPerSM + warps / 2) / warps;
+    if (ctas < 1) ctas = 1;
+    const size_t cap = sm_smem > 0 ? (size_t)sm_smem / ctas - 2048 : 0;
+    if (cap > smem && cap <= 200 * 1024) smem = cap;
+  }
   // per instantiation; static shared memory counts against the same 48 KB
   // default, so the attribute is set whatever the dynamic size
   static bool attr_set = false;
