@@ -468,9 +468,12 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   __syncthreads();
   } else {
     // Short code (native arithmetic): the thread's own t-fiber stays in
-    // registers from D_t x through the geometry to D_t^T t, so x is never
-    // overwritten before the transposed passes (one barrier fewer) and the
-    // t values make no shared-memory round trips.
+    // registers from D_t x through the geometry to D_t^T t (no shared-memory
+    // round trips, x never overwritten); the r- and s-fiber transposed
+    // products overwrite B0 and B1 in place (no read-modify-write of Y, no
+    // barrier between them); the t-fiber owner sums Y = Y_t + Y_r + Y_s at
+    // its nodes and stores it to HBM (for each k the warp writes consecutive
+    // i, j: coalesced).
     forward(0);
     forward(1);
     V tf[N1];
@@ -481,6 +484,7 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
       contract<P, N1>(eoD, fin_, tf);
     }
     __syncthreads();  // every r/s fiber product is in B0, B1
+    V yt[N1];
     {
       const int i = qa, j = qb;
       Geometry<P, N1, KIND> gm;
@@ -500,17 +504,33 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
         s_e[sidx] = P::st(o3[1]);
         tf[k] = o3[2];
       }
-      V yt[N1];
       contract<P, N1>(eoDT, tf, yt);
-#pragma unroll
-      for (int n = 0; n < N1; ++n) x_e[ft + n * str_t] = P::st(yt[n]);
     }
+    __syncthreads();  // every r, s value is in B0, B1
 #pragma unroll
-    for (int ph = 4; ph < 6; ++ph) transposed(ph);
-    __syncthreads();
+    for (int d = 0; d < 2; ++d) {
+      S *buf = d == 0 ? r_e : s_e;
+      const int base = d == 0 ? fr : fs, stride = d == 0 ? str_r : str_s;
+      V fin_[N1], fout[N1];
+#pragma unroll
+      for (int n = 0; n < N1; ++n) fin_[n] = P::ld(buf + base + n * stride);
+      contract<P, N1>(eoDT, fin_, fout);
+#pragma unroll
+      for (int n = 0; n < N1; ++n) buf[base + n * stride] = P::st(fout[n]);
+    }
+    __syncthreads();  // every Y_r, Y_s value is in B0, B1
+    if (live) {
+      typename P::IO *ye = Y + e * n3 + qa + N1 * qb;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const int sidx = ft + k * str_t;
+        ye[k * N1 * N1] = P::to_io(P::add(P::add(yt[k], P::ld(r_e + sidx)), P::ld(s_e + sidx)));
+      }
+    }
   }
 
-  // pass 5: Y to HBM
+  // pass 5: Y to HBM (long-code path; the short-code path stored it above)
+  if constexpr (P::kRoll)
   for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
     typename P::IO *dst = Y + e0 * n3 + (int64_t)row * N1;
     const S *src = xs + row * Sh::P;

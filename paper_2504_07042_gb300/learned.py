@@ -76,7 +76,7 @@ def train_select(mlp, F, T, op_val, b_val, chunks=(3, 3, 3, 3, 4, 4), omegas=(0.
     """Train in chunks of epochs and keep the checkpoint and damping omega that
     solve a held-out validation problem (op_val, b_val: another source on a
     mesh with gs_setup) in the fewest flexible-PCG iterations, without the
-    Jacobi fallback.  The network's only judge is the solver it serves: a
+    Jacobi fallback.  The solver the network serves is what decides: a
     lower training loss does not by itself mean fewer iterations.
     Returns (omega, validation iterations, loss history, trace of (epochs, omega, iterations))."""
     import torch
