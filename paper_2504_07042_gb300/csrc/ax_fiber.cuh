@@ -403,8 +403,9 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   //   ph 0: r-fibers  D x -> B0 (x0)     ph 1: s-fibers  D x -> B1 (x1)
   //   ph 2: t-fiber   D x -> X  (x2);  then per node the geometry and
   //         (r,s,t) = G (x0,x1,x2): r -> B0, s -> B1, t -> X
-  //   ph 3: t-fiber   D^T t -> X (Y)   ph 4: r-fibers Y += D^T r
-  //   ph 5: s-fibers  Y += D^T s
+  //   ph 3: t-fiber   D^T t -> registers (Y_t)
+  //   ph 4: r-fibers  D^T r -> B0 (Y_r)  ph 5: s-fibers  D^T s -> B1 (Y_s)
+  //   then the t-fiber owner stores Y = Y_t + Y_r + Y_s to HBM
   const int fr = Sh::at(0, qa, qb), fs = Sh::at(qa, 0, qb), ft = Sh::at(qa, qb, 0);
   constexpr int str_r = 1, str_s = Sh::P, str_t = Sh::P * N1;
   auto forward = [&](int ph) {
@@ -418,24 +419,6 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     contract<P, N1>(eoD, fin_, fout);
 #pragma unroll
     for (int n = 0; n < N1; ++n) dst[base + n * stride] = P::st(fout[n]);
-  };
-  auto transposed = [&](int ph) {
-    if (ph >= 4) __syncthreads();  // ph 4: all r, s written; ph 5: Y updates of ph 4 done
-    const S *src = ph == 3 ? x_e : (ph == 4 ? r_e : s_e);
-    const int base = ph == 3 ? ft : (ph == 4 ? fr : fs);
-    const int stride = ph == 3 ? str_t : (ph == 4 ? str_r : str_s);
-    V fin_[N1], fout[N1];
-#pragma unroll
-    for (int n = 0; n < N1; ++n) fin_[n] = P::ld(src + base + n * stride);
-    contract<P, N1>(eoDT, fin_, fout);
-    if (ph == 3) {
-#pragma unroll
-      for (int n = 0; n < N1; ++n) x_e[base + n * stride] = P::st(fout[n]);
-    } else {
-#pragma unroll
-      for (int n = 0; n < N1; ++n)
-        x_e[base + n * stride] = P::st(P::add(P::ld(x_e + base + n * stride), fout[n]));
-    }
   };
   if constexpr (P::kRoll) {
 #pragma unroll 1
@@ -463,9 +446,37 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
 #pragma unroll 1
     for (int k = 0; k < N1; ++k) node(k);
   }
+    // transposed products: D_t^T t of the own t-fiber into registers, then
+    // the r- and s-fibers in place in B0, B1 (one rolled loop: one code
+    // copy of the D^T product); the t-fiber owner sums and stores Y
+    V yt[N1];
 #pragma unroll 1
-    for (int ph = 3; ph < 6; ++ph) transposed(ph);
-  __syncthreads();
+    for (int ph = 3; ph < 6; ++ph) {
+      if (ph == 4) __syncthreads();  // every thread's r, s values are in B0, B1
+      S *buf = ph == 3 ? x_e : (ph == 4 ? r_e : s_e);
+      const int base = ph == 3 ? ft : (ph == 4 ? fr : fs);
+      const int stride = ph == 3 ? str_t : (ph == 4 ? str_r : str_s);
+      V fin_[N1], fout[N1];
+#pragma unroll
+      for (int n = 0; n < N1; ++n) fin_[n] = P::ld(buf + base + n * stride);
+      contract<P, N1>(eoDT, fin_, fout);
+      if (ph == 3) {
+#pragma unroll
+        for (int n = 0; n < N1; ++n) yt[n] = fout[n];
+      } else {
+#pragma unroll
+        for (int n = 0; n < N1; ++n) buf[base + n * stride] = P::st(fout[n]);
+      }
+    }
+    __syncthreads();  // every Y_r, Y_s value is in B0, B1
+    if (live) {
+      typename P::IO *ye = Y + e * n3 + qa + N1 * qb;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const int sidx = ft + k * str_t;
+        ye[k * N1 * N1] = P::to_io(P::add(P::add(yt[k], P::ld(r_e + sidx)), P::ld(s_e + sidx)));
+      }
+    }
   } else {
     // Short code (native arithmetic): the thread's own t-fiber stays in
     // registers from D_t x through the geometry to D_t^T t (no shared-memory
@@ -529,14 +540,6 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     }
   }
 
-  // pass 5: Y to HBM (long-code path; the short-code path stored it above)
-  if constexpr (P::kRoll)
-  for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
-    typename P::IO *dst = Y + e0 * n3 + (int64_t)row * N1;
-    const S *src = xs + row * Sh::P;
-#pragma unroll
-    for (int i = 0; i < N1; ++i) dst[i] = P::to_io(P::ld(src + i));
-  }
   __syncthreads();  // the next block reuses the shared buffers
   }
 }
