@@ -181,6 +181,14 @@ template <class P, int N1, int KIND>
 constexpr bool kFillWarps =
     KIND != AX_GEOM_STORED && (N1 == 6 || (sizeof(typename P::S) == 8 && KIND != AX_GEOM_PARALLELEPIPED));
 
+// Minimum resident CTAs for the register budget (0: no bound): the
+// double-word kernels at N1 = 16 (256-thread CTAs) are held to 128 registers
+// so that two CTAs fit per SM (unbounded they take about 147 and run one CTA
+// per SM, 5-30% slower).  Elsewhere no bound is given: even an explicit 1
+// changes the register allocation for the worse.
+template <class P, int N1, int KIND>
+constexpr int kMinCtas = (P::kRoll && N1 == 16) ? 2 : 0;
+
 template <int N1, int EM = 1, bool FILL = false>
 struct Shape {
   static constexpr int n3 = N1 * N1 * N1;
@@ -352,7 +360,7 @@ struct GeoWords {
 //   c_eoD / c_eoDT: even-odd blocks of D and D^T, c_w, c_x: weights, points.
 // ---------------------------------------------------------------------------
 template <class P, int N1, int KIND, int EM>
-__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads)
+__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads, kMinCtas<P, N1, KIND>)
     ax_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
                     const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y) {
   using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
@@ -446,10 +454,13 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
 #pragma unroll 1
     for (int k = 0; k < N1; ++k) node(k);
   }
-    // transposed products: D_t^T t of the own t-fiber into registers, then
-    // the r- and s-fibers in place in B0, B1 (one rolled loop: one code
-    // copy of the D^T product); the t-fiber owner sums and stores Y
-    V yt[N1];
+    // transposed products: D_t^T t of the own t-fiber, then the r- and
+    // s-fibers in place in B0, B1 (one rolled loop: one code copy of the D^T
+    // product); the t-fiber owner sums and stores Y.  Y_t stays in registers
+    // up to N1 = 10; above, the 2 N1 extra registers would cost resident
+    // warps, so it goes back in place into X (read only by its owner).
+    constexpr bool kYtRegs = N1 <= 10;
+    V yt[kYtRegs ? N1 : 1];
 #pragma unroll 1
     for (int ph = 3; ph < 6; ++ph) {
       if (ph == 4) __syncthreads();  // every thread's r, s values are in B0, B1
@@ -460,9 +471,9 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(buf + base + n * stride);
       contract<P, N1>(eoDT, fin_, fout);
-      if (ph == 3) {
+      if (kYtRegs && ph == 3) {
 #pragma unroll
-        for (int n = 0; n < N1; ++n) yt[n] = fout[n];
+        for (int n = 0; n < N1; ++n) yt[kYtRegs ? n : 0] = fout[n];
       } else {
 #pragma unroll
         for (int n = 0; n < N1; ++n) buf[base + n * stride] = P::st(fout[n]);
@@ -474,7 +485,8 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
-        ye[k * N1 * N1] = P::to_io(P::add(P::add(yt[k], P::ld(r_e + sidx)), P::ld(s_e + sidx)));
+        const V ytk = kYtRegs ? yt[kYtRegs ? k : 0] : P::ld(x_e + sidx);
+        ye[k * N1 * N1] = P::to_io(P::add(P::add(ytk, P::ld(r_e + sidx)), P::ld(s_e + sidx)));
       }
     }
   } else {
