@@ -52,11 +52,19 @@ struct Native {
   __device__ static __forceinline__ IO to_io(V v) { return v; }
   __device__ static __forceinline__ V lit(double v) { return (T)v; }
   __device__ static __forceinline__ A zero() { return T(0); }
+  __device__ static __forceinline__ A mul0(V x, V y) { return x * y; }
   __device__ static __forceinline__ void mac(A &a, V x, V y) { a = fma(x, y, a); }
   __device__ static __forceinline__ V fin(A a) { return a; }
+  __device__ static __forceinline__ V acc_sum(A a, A b) { return a + b; }
+  __device__ static __forceinline__ V acc_dif(A a, A b) { return a - b; }
   __device__ static __forceinline__ V add(V a, V b) { return a + b; }
   __device__ static __forceinline__ V sub(V a, V b) { return a - b; }
+  __device__ static __forceinline__ V add_lazy(V a, V b) { return a + b; }
+  __device__ static __forceinline__ V sub_lazy(V a, V b) { return a - b; }
   __device__ static __forceinline__ V mul(V a, V b) { return a * b; }
+  __device__ static __forceinline__ V fma3(V a, V b, V c) { return fma(a, b, c); }
+  __device__ static __forceinline__ V twice(V a) { return a + a; }
+  __device__ static __forceinline__ IO sum3_io(V a, V b, V c) { return (a + b) + c; }
   __device__ static __forceinline__ V div(V a, V b) {
     if constexpr (sizeof(T) == 4)
       return __fdividef(a, b);  // 2-ulp quotient: the FP32 path's tolerance is 2e-5
@@ -87,11 +95,20 @@ struct DW {
   __device__ static __forceinline__ IO to_io(V v) { return dw::to_double(v); }
   __device__ static __forceinline__ V lit(double v) { return dw::make((float)v, 0.0f); }  // exact small literals only
   __device__ static __forceinline__ A zero() { return dw::acc_zero(); }
+  __device__ static __forceinline__ A mul0(V x, V y) { return dw::mul_acc(x, y); }
   __device__ static __forceinline__ void mac(A &a, V x, V y) { dw::mac(a, x, y); }
   __device__ static __forceinline__ V fin(A a) { return dw::fin(a); }
+  // sums that feed only error-tolerant consumers skip the final Fast2Sum (dw.cuh)
+  __device__ static __forceinline__ V acc_sum(A a, A b) { return dw::acc_sum(a, b); }
+  __device__ static __forceinline__ V acc_dif(A a, A b) { return dw::acc_dif(a, b); }
   __device__ static __forceinline__ V add(V a, V b) { return dw::add(a, b); }
   __device__ static __forceinline__ V sub(V a, V b) { return dw::sub(a, b); }
+  __device__ static __forceinline__ V add_lazy(V a, V b) { return dw::add_lazy(a, b); }
+  __device__ static __forceinline__ V sub_lazy(V a, V b) { return dw::sub_lazy(a, b); }
   __device__ static __forceinline__ V mul(V a, V b) { return dw::mul(a, b); }
+  __device__ static __forceinline__ V fma3(V a, V b, V c) { return dw::fma(a, b, c); }
+  __device__ static __forceinline__ V twice(V a) { return dw::make(2.0f * a.hi, 2.0f * a.lo); }  // exact
+  __device__ static __forceinline__ IO sum3_io(V a, V b, V c) { return dw::sum3_to_double(a, b, c); }
   __device__ static __forceinline__ V div(V a, V b) { return dw::div(a, b); }
   __device__ static __forceinline__ V neg(V a) { return dw::neg(a); }
 };
@@ -99,8 +116,7 @@ struct DW {
 
 template <class P>
 __device__ __forceinline__ typename P::V dot3(const typename P::V a[3], const typename P::V b[3]) {
-  typename P::A s = P::zero();
-  P::mac(s, a[0], b[0]);
+  typename P::A s = P::mul0(a[0], b[0]);
   P::mac(s, a[1], b[1]);
   P::mac(s, a[2], b[2]);
   return P::fin(s);
@@ -109,8 +125,7 @@ __device__ __forceinline__ typename P::V dot3(const typename P::V a[3], const ty
 // a*b - c*d
 template <class P>
 __device__ __forceinline__ typename P::V det2(typename P::V a, typename P::V b, typename P::V c, typename P::V d) {
-  typename P::A s = P::zero();
-  P::mac(s, a, b);
+  typename P::A s = P::mul0(a, b);
   P::mac(s, P::neg(c), d);
   return P::fin(s);
 }
@@ -133,26 +148,33 @@ __device__ __forceinline__ void contract(const typename P::C *__restrict__ eo, c
   V e[c], o[c];
 #pragma unroll
   for (int m = 0; m < c; ++m) {
-    e[m] = P::add(in[m], in[N1 - 1 - m]);
-    o[m] = P::sub(in[m], in[N1 - 1 - m]);
+    e[m] = P::add_lazy(in[m], in[N1 - 1 - m]);
+    o[m] = P::sub_lazy(in[m], in[N1 - 1 - m]);
   }
 #pragma unroll
   for (int i = 0; i < c; ++i) {
-    typename P::A p = P::zero(), q = P::zero();
+    typename P::A p = P::mul0(P::cst(eo + i * N1), e[0]), q = P::mul0(P::cst(eo + i * N1 + c), o[0]);
 #pragma unroll
-    for (int m = 0; m < c; ++m) {
+    for (int m = 1; m < c; ++m) {
       P::mac(p, P::cst(eo + i * N1 + m), e[m]);
       P::mac(q, P::cst(eo + i * N1 + c + m), o[m]);
     }
     if constexpr (odd) P::mac(p, P::cst(eo + i * N1 + 2 * c), in[c]);
-    const V Pv = P::fin(p), Qv = P::fin(q);
-    out[i] = P::add(Pv, Qv);
-    out[N1 - 1 - i] = P::sub(Qv, Pv);
+    if constexpr (N1 < 16) {
+      out[i] = P::acc_sum(p, q);
+      out[N1 - 1 - i] = P::acc_dif(q, p);
+    } else {
+      // N1 = 16: under the 128-register cap the sums straight from the
+      // accumulators spill in double-word arithmetic; finalise them first
+      const V Pv = P::fin(p), Qv = P::fin(q);
+      out[i] = P::add(Pv, Qv);
+      out[N1 - 1 - i] = P::sub(Qv, Pv);
+    }
   }
   if constexpr (odd) {
-    typename P::A q = P::zero();
+    typename P::A q = P::mul0(P::cst(eo + c * N1), o[0]);
 #pragma unroll
-    for (int m = 0; m < c; ++m) P::mac(q, P::cst(eo + c * N1 + m), o[m]);
+    for (int m = 1; m < c; ++m) P::mac(q, P::cst(eo + c * N1 + m), o[m]);
     out[c] = P::fin(q);
   }
 }
@@ -240,18 +262,17 @@ struct Geometry {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         auto M = [&](int m) { return P::ld(sv + 3 * m + c); };  // A B C D E F G = 0..6
-        E0[c] = P::add(M(0), P::mul(M(3), s));
-        E1[c] = P::add(M(4), P::mul(M(6), s));
-        F0[c] = P::add(M(1), P::mul(M(3), r));
-        F1[c] = P::add(M(5), P::mul(M(6), r));
-        typename P::A q = P::zero();
-        P::mac(q, M(4), r);
+        E0[c] = P::fma3(M(3), s, M(0));
+        E1[c] = P::fma3(M(6), s, M(4));
+        F0[c] = P::fma3(M(3), r, M(1));
+        F1[c] = P::fma3(M(6), r, M(5));
+        typename P::A q = P::mul0(M(4), r);
         P::mac(q, M(5), s);
         P::mac(q, M(6), rs);
         J2[c] = P::add(M(2), P::fin(q));
       }
-      k00[0] = dot3<P>(E0, E0); k00[1] = P::add(dot3<P>(E0, E1), dot3<P>(E0, E1)); k00[2] = dot3<P>(E1, E1);
-      k11[0] = dot3<P>(F0, F0); k11[1] = P::add(dot3<P>(F0, F1), dot3<P>(F0, F1)); k11[2] = dot3<P>(F1, F1);
+      k00[0] = dot3<P>(E0, E0); k00[1] = P::twice(dot3<P>(E0, E1)); k00[2] = dot3<P>(E1, E1);
+      k11[0] = dot3<P>(F0, F0); k11[1] = P::twice(dot3<P>(F0, F1)); k11[2] = dot3<P>(F1, F1);
       // K = J^T J as polynomials in t
       k01[0] = dot3<P>(E0, F0); k01[1] = P::add(dot3<P>(E0, F1), dot3<P>(E1, F0)); k01[2] = dot3<P>(E1, F1);
       k02[0] = dot3<P>(E0, J2); k02[1] = dot3<P>(E1, J2);
@@ -274,8 +295,8 @@ struct Geometry {
     }
   }
 
-  __device__ __forceinline__ static V quad(const V c[3], V t) { return P::add(c[0], P::mul(t, P::add(c[1], P::mul(t, c[2])))); }
-  __device__ __forceinline__ static V lin(const V c[2], V t) { return P::add(c[0], P::mul(t, c[1])); }
+  __device__ __forceinline__ static V quad(const V c[3], V t) { return P::fma3(t, P::fma3(t, c[2], c[1]), c[0]); }
+  __device__ __forceinline__ static V lin(const V c[2], V t) { return P::fma3(t, c[1], c[0]); }
 
   // adjugate of K at t (symmetric: A00 A01 A02 A11 A12 A22)
   __device__ __forceinline__ void adjK(V t, V A[6]) const {
@@ -486,7 +507,7 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
         const V ytk = kYtRegs ? yt[kYtRegs ? k : 0] : P::ld(x_e + sidx);
-        ye[k * N1 * N1] = P::to_io(P::add(P::add(ytk, P::ld(r_e + sidx)), P::ld(s_e + sidx)));
+        ye[k * N1 * N1] = P::sum3_io(ytk, P::ld(r_e + sidx), P::ld(s_e + sidx));
       }
     }
   } else {
@@ -547,7 +568,7 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
-        ye[k * N1 * N1] = P::to_io(P::add(P::add(yt[k], P::ld(r_e + sidx)), P::ld(s_e + sidx)));
+        ye[k * N1 * N1] = P::sum3_io(yt[k], P::ld(r_e + sidx), P::ld(s_e + sidx));
       }
     }
   }
