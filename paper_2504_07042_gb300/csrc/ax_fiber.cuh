@@ -84,10 +84,11 @@ struct DW {
   static constexpr int kTiles = 1;
   // Resident warps per SM the launcher aims at for the trilinear kinds at
   // N1 = 8 (by padding the dynamic shared memory): more warps thrash the
-  // instruction cache with this long code (measured on GB300: 4 CTAs of 4
-  // warps 8% faster than the 7 that registers allow; at other orders and for
-  // the stored kind the cap measured slower, so it is not applied there).
-  static constexpr int kTargetWarpsPerSM = 16;
+  // instruction cache with this long code.  Measured on GB300: 5 CTAs of 4
+  // warps 2% faster than 4, and fewer (3) or longer code per warp (unrolled
+  // k or phase loops) slower; at other orders and for the stored kind a cap
+  // measured slower, so it is not applied there.
+  static constexpr int kTargetWarpsPerSM = 20;
   __device__ static __forceinline__ V ld(const S *p) { return dw::from_float2(*p); }
   __device__ static __forceinline__ S st(V v) { return make_float2(v.hi, v.lo); }
   __device__ static __forceinline__ V cst(const C *p) { return dw::from_float2(*p); }
