@@ -87,7 +87,10 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
 
 /* AxLocal (Algorithm 1, Poisson: lambda0 = 1, lambda1 = 0):
  *   Y[e] = A^(e) X[e] = D^T (w G) D X[e] for every element (unassembled).
- *   X, Y: device, [E][n3], float64 for AX_FP64/AX_F64DW, float32 otherwise.
+ *   X, Y: device, [E][n3], float64 for AX_FP64/AX_F64DW, float32 otherwise,
+ *   aligned to their element size (a 16-byte aligned X is read in 16-byte
+ *   vectors where the kernel does so; any other X takes word loads and gives
+ *   the same result bit for bit).
  *   Y is overwritten; X and Y must not overlap.  One kernel launch. */
 ax_status ax_local(ax_ctx *c, const void *X, void *Y, void *stream);
 

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "ax_internal.h"
 #include "dw.cuh"
@@ -372,6 +373,44 @@ struct Geometry {
 };
 
 
+// Coalesced copy of a block of values (contiguous in HBM) into padded
+// shared-memory rows of N1 values (pitch PITCH), converted by the policy P:
+// value m goes to row m / N1 at i = m % N1.  Consecutive threads read
+// consecutive 16-byte vectors when the values come in whole vectors and the
+// pointer is 16-byte aligned, else consecutive words.  THREADS * N1 >= nvals.
+template <class P, int N1, int PITCH, int THREADS>
+__device__ __forceinline__ void load_rows(const typename P::IO *__restrict__ src, int nvals, typename P::S *xs,
+                                          int tid) {
+  using IO = typename P::IO;
+  constexpr int n3 = N1 * N1 * N1, VEC = 16 / (int)sizeof(IO);
+  auto put = [&](int m, IO v) {
+    const int row = m / N1;
+    xs[row * PITCH + (m - row * N1)] = P::st(P::from_io(v));
+  };
+  if constexpr (n3 % VEC == 0) {
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+      using VT = typename std::conditional<sizeof(IO) == 4, float4, double2>::type;
+      const VT *srcv = reinterpret_cast<const VT *>(src);
+#pragma unroll
+      for (int s = 0; s < (N1 + VEC - 1) / VEC; ++s) {
+        const int mv = tid + s * THREADS;
+        if (mv * VEC < nvals) {
+          const VT v = srcv[mv];
+          const IO *pv = reinterpret_cast<const IO *>(&v);
+#pragma unroll
+          for (int c = 0; c < VEC; ++c) put(mv * VEC + c, pv[c]);
+        }
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < N1; ++s) {
+    const int m = tid + s * THREADS;
+    if (m < nvals) put(m, src[m]);
+  }
+}
+
 template <int KIND>
 struct GeoWords {
   static constexpr int value = (KIND == AX_GEOM_STORED) ? 0 : (KIND == AX_GEOM_PARALLELEPIPED ? kParWords : kVertexWords);
@@ -412,14 +451,30 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   const int64_t e = e0 + z;
   const bool live = z < nel;
 
-  // pass 0: the CTA's elements (contiguous in HBM) into padded shared memory,
-  // one i-row of N1 values per thread and step (row = j + N1 (k + N1 z) is
-  // also the padded row index: padded offset = row * P)
-  for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
-    const typename P::IO *src = X + e0 * n3 + (int64_t)row * N1;
-    S *dst = xs + row * Sh::P;
+  // pass 0: the CTA's elements (contiguous in HBM) into padded shared memory.
+  // Value m of the block sits in row m / N1 (row = j + N1 (k + N1 z) is also
+  // the padded row index) at i = m % N1.  Float32 data at N1 = 2, 4, 8 and
+  // double-word data at N1 = 16 are read coalesced (load_rows): measured on
+  // GB300 4-16% faster than one row per thread for float32 at N = 3 and 7,
+  // 3-10% for double-word at N = 15.  Elsewhere one i-row of N1 values per
+  // thread: the coalesced form measured 10% slower for float32 N = 5 (the
+  // row and column of each value cost a division there), 2% slower for
+  // double-word N = 7 and, through a register increase that halves the
+  // resident CTAs, 23% slower for float32 N = 15 (the compiler raises the
+  // register count at every N1 >= 11 of the float32 kernels with it).
+  {
+    using IO = typename P::IO;
+    const IO *src = X + e0 * n3;
+    if constexpr ((sizeof(IO) == 4 && (N1 == 2 || N1 == 4 || N1 == 8)) || (P::kRoll && N1 == 16)) {
+      load_rows<P, N1, Sh::P, Sh::threads>(src, nel * n3, xs, tid);
+    } else {
+      for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
+        const IO *srow = src + (int64_t)row * N1;
+        S *dst = xs + row * Sh::P;
 #pragma unroll
-    for (int i = 0; i < N1; ++i) dst[i] = P::st(P::from_io(src[i]));
+        for (int i = 0; i < N1; ++i) dst[i] = P::st(P::from_io(srow[i]));
+      }
+    }
   }
   if constexpr (GW > 0) {
     for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];

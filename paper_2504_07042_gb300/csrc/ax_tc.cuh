@@ -191,12 +191,18 @@ __global__ void __launch_bounds__(TcShape<N1>::threads)
   for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     const int64_t e0 = blk * EPB;
     const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
-    // X rows into the padded element (row = j + N1 (k + N1 z) is also the padded row)
-    for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
-      const float *src = X + e0 * n3 + (int64_t)row * N1;
-      float *dst = xs + row * Sh::P;
+    // X into the padded element (row = j + N1 (k + N1 z) is also the padded
+    // row): coalesced at N1 = 2, 4, 8 (row and column by shifts), one row per
+    // thread elsewhere (the same rule as the fiber kernels, measured there)
+    if constexpr (N1 == 2 || N1 == 4 || N1 == 8) {
+      fiber::load_rows<P, N1, Sh::P, Sh::threads>(X + e0 * n3, nel * n3, xs, tid);
+    } else {
+      for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
+        const float *src = X + e0 * n3 + (int64_t)row * N1;
+        float *dst = xs + row * Sh::P;
 #pragma unroll
-      for (int i = 0; i < N1; ++i) dst[i] = src[i];
+        for (int i = 0; i < N1; ++i) dst[i] = src[i];
+      }
     }
     if constexpr (GW > 0) {
       for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
@@ -238,15 +244,27 @@ __global__ void __launch_bounds__(TcShape<N1>::threads)
         if (z < nel) unit<MODE, N1>(buf, buf, d, ft, lane, bt);
       }
     __syncthreads();
-    // Y = b0 + b1 + b2 to HBM
-    for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
-      float *dst = Y + e0 * n3 + (int64_t)row * N1;
-      const int z = row / (N1 * N1);
-      const int off = row * Sh::P;
-      const float *y0 = bb + off, *y1 = bb + EPB * ES + off, *y2 = bb + 2 * EPB * ES + off;
-      (void)z;
+    // Y = b0 + b1 + b2 to HBM (coalesced at N1 = 2, 4, 8: value m of the
+    // block from row m / N1 at i = m % N1)
+    if constexpr (N1 == 2 || N1 == 4 || N1 == 8) {
+      float *dst = Y + e0 * n3;
+      const int nvals = nel * n3;
+#pragma unroll 4
+      for (int s = 0; s < N1; ++s) {
+        const int m = tid + s * Sh::threads;
+        if (m < nvals) {
+          const int row = m / N1, off = row * Sh::P + (m - row * N1);
+          dst[m] = bb[off] + bb[EPB * ES + off] + bb[2 * EPB * ES + off];
+        }
+      }
+    } else {
+      for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
+        float *dst = Y + e0 * n3 + (int64_t)row * N1;
+        const int off = row * Sh::P;
+        const float *y0 = bb + off, *y1 = bb + EPB * ES + off, *y2 = bb + 2 * EPB * ES + off;
 #pragma unroll
-      for (int i = 0; i < N1; ++i) dst[i] = y0[i] + y1[i] + y2[i];
+        for (int i = 0; i < N1; ++i) dst[i] = y0[i] + y1[i] + y2[i];
+      }
     }
     __syncthreads();  // the next block reuses the shared buffers
   }

@@ -107,6 +107,26 @@ def test_tensor_core_every_order(ax, orc, kind, prec, N):
     assert err <= TOL[prec]
 
 
+@pytest.mark.parametrize("N,prec", [(3, "fp32"), (7, "fp32"), (5, "tf32"), (7, "bf16"), (15, "f64dw"), (6, "fp32")])
+def test_unaligned_x_takes_word_loads(ax, N, prec):
+    # X (and Y) one element past a 16-byte boundary: the kernels that read 16-byte
+    # vectors from an aligned X fall back to word loads, with identical results
+    dev = torch.device("cuda:0")
+    V = _mesh("trilinear", 3, 2, 2)
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, "trilinear", prec)
+    X = torch.from_numpy(inputs.element_vectors(V.shape[0], N, seed=3)).to(dev, op.dtype)
+    Ya = torch.full_like(X, float("nan"))
+    op.ax_local(X, Ya)
+    buf = torch.full((2, X.numel() + 1), float("nan"), dtype=op.dtype, device=dev)
+    Xu, Yu = buf[0, 1:].view_as(X), buf[1, 1:].view_as(X)
+    Xu.copy_(X)
+    assert Xu.data_ptr() % 16 != 0
+    op.ax_local(Xu, Yu)
+    torch.cuda.synchronize()
+    assert torch.equal(Ya, Yu)
+    op.ax_destroy()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "f64dw"])
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("N", [1, 3, 7, 15])
