@@ -33,13 +33,25 @@ double pipe_ops_per_node(int N1, int kind, int prec) {
   ops += 3.0 * dot3;                      // (r, s, t) = G (x0, x1, x2)
   ops += dwp ? 17.0 : 2.0;                // Y = Y_t + Y_r + Y_s (two TwoSums and the low parts)
   // trilinear geometry (Algorithm 2 with K = J^T J and det J as polynomials in t):
-  // per thread (i,j), from the record's monomial coefficients: E0/E1/F0/F1
-  // (12 multiply-adds), J2 (a 3-term dot product plus C), the 13 dot
-  // products of the K coefficients (the t-terms of K00 and K11 doubled
-  // exactly) and, for det J, 6 two-term determinants and 4 dot products,
-  // amortised over the N1 nodes of its fiber
-  const double cols = 12.0 * fma + 3.0 * (dot3 + add) + mul;
-  const double coeffs = 13.0 * dot3 + add, det_coeffs = 6.0 * det2 + 4.0 * dot3 + add;
+  // per thread (i,j), from the record's monomial coefficients: J2 (a 3-term
+  // dot product plus C, and rs), the axis terms E0/E1 with the K00
+  // coefficients (per s) and F0/F1 with the K11 coefficients (per r): 12
+  // multiply-adds, 6 dot products, 2 exact doublings; the 9 dot products of
+  // the K01, K02, K12, K22 coefficients and, for det J, 6 two-term
+  // determinants and 4 dot products; all amortised over the N1 nodes of the
+  // thread's fiber.  Where the kernel shares the axis terms (native FP64;
+  // double-word up to N1 = 5) the first 2 N1 threads of an element compute
+  // them once, counted as the whole warps that run them (an element's share
+  // of a warp below 32 threads per element).
+  const bool share = (kind == AX_GEOM_TRILINEAR || kind == AX_GEOM_TRILINEAR_PARTIAL) &&
+                     (dwp ? N1 <= 5 : prec == AX_FP64);
+  const double twice = dwp ? 2.0 : 1.0;
+  const double axis_set = 6.0 * fma + 3.0 * dot3 + twice;  // one r- or s-axis set
+  const int F = N1 * N1;
+  const double axis_lanes = F < 32 ? F : 32.0 * ((2 * N1 + 31) / 32);
+  const double axis = share ? axis_lanes * axis_set / F : 2.0 * axis_set;  // per thread
+  const double cols = 3.0 * (dot3 + add) + mul;
+  const double coeffs = 9.0 * dot3 + add + axis, det_coeffs = 6.0 * det2 + 4.0 * dot3 + add;
   const double quad = 2.0 * fma, lin = fma;
   const double knode = 3.0 * quad + 2.0 * lin, adj = 6.0 * det2, scale = 3.0 * mul;
   switch (kind) {

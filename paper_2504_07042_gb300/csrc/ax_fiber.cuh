@@ -213,6 +213,15 @@ constexpr bool kFillWarps =
 template <class P, int N1, int KIND>
 constexpr int kMinCtas = (P::kRoll && N1 == 16) ? 2 : 0;
 
+// Trilinear kinds: whether an element's first 2 N1 threads compute the axis
+// terms of the geometry (Geometry::axis_terms) for all its threads.  Measured
+// on GB300: native FP64 3% faster (N = 7), double-word 7% faster at N = 3 but
+// 1-4% slower at N = 7 (where the prologue is amortised over more nodes),
+// FP32 1-3% slower; so native FP64 at every order, double-word up to N1 = 5.
+template <class P, int N1, int KIND>
+constexpr bool kShareAxis = (KIND == AX_GEOM_TRILINEAR || KIND == AX_GEOM_TRILINEAR_PARTIAL) &&
+                            (P::kRoll ? N1 <= 5 : sizeof(typename P::V) == 8);
+
 template <int N1, int EM = 1, bool FILL = false>
 struct Shape {
   static constexpr int n3 = N1 * N1 * N1;
@@ -247,8 +256,35 @@ struct Geometry {
   V h[7];
   const S *gl = nullptr;
 
+  // Terms of the trilinear geometry that depend on one reference coordinate
+  // only, written to out[0..8]:  axis 0 (u = r = xi_idx): F0 = B + D r,
+  // F1 = F + G r and the K11 coefficients (F0.F0, 2 F0.F1, F1.F1);  axis 1
+  // (u = s = xi_idx): E0 = A + D s, E1 = E + G s and the K00 coefficients.
+  // An element has N1 of each, which its first 2 N1 threads compute once and
+  // share (kAxisWords words per set) instead of every thread recomputing them.
+  static constexpr int kAxisWords = 9;
+  __device__ __forceinline__ static void axis_terms(const S *sv, const typename P::C *xg, int axis, int idx,
+                                                    S *out) {
+    const V u = P::cst(xg + idx);
+    V X0[3], X1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      auto M = [&](int m) { return P::ld(sv + 3 * m + c); };  // A B C D E F G = 0..6
+      X0[c] = P::fma3(M(3), u, M(axis ? 0 : 1));
+      X1[c] = P::fma3(M(6), u, M(axis ? 4 : 5));
+      out[c] = P::st(X0[c]);
+      out[3 + c] = P::st(X1[c]);
+    }
+    out[6] = P::st(dot3<P>(X0, X0));
+    out[7] = P::st(P::twice(dot3<P>(X0, X1)));
+    out[8] = P::st(dot3<P>(X1, X1));
+  }
+
+  // AX: read the axis terms from ax, the element's shared table
+  // ([2][N1][kAxisWords], see axis_terms), instead of computing them here.
+  template <bool AX = false>
   __device__ __forceinline__ void prologue(const S *sv, const typename P::C *xg, const typename P::C *wg, int i,
-                                           int j, const S *G_e, const S *lam_e) {
+                                           int j, const S *G_e, const S *lam_e, const S *ax = nullptr) {
     wij = P::mul(P::cst(wg + i), P::cst(wg + j));
     if constexpr (KIND == AX_GEOM_STORED) {
       gl = G_e;
@@ -261,20 +297,33 @@ struct Geometry {
       // F1 = F + G r;  J2 = C + E r + F s + G rs   (r = xi_i, s = xi_j)
       V E0[3], E1[3], F0[3], F1[3], J2[3];
       const V r = P::cst(xg + i), s = P::cst(xg + j), rs = P::mul(r, s);
+      if constexpr (AX) {
+        const S *fi = ax + i * kAxisWords, *ej = ax + (N1 + j) * kAxisWords;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          F0[c] = P::ld(fi + c); F1[c] = P::ld(fi + 3 + c);
+          E0[c] = P::ld(ej + c); E1[c] = P::ld(ej + 3 + c);
+          k11[c] = P::ld(fi + 6 + c); k00[c] = P::ld(ej + 6 + c);
+        }
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         auto M = [&](int m) { return P::ld(sv + 3 * m + c); };  // A B C D E F G = 0..6
-        E0[c] = P::fma3(M(3), s, M(0));
-        E1[c] = P::fma3(M(6), s, M(4));
-        F0[c] = P::fma3(M(3), r, M(1));
-        F1[c] = P::fma3(M(6), r, M(5));
+        if constexpr (!AX) {
+          E0[c] = P::fma3(M(3), s, M(0));
+          E1[c] = P::fma3(M(6), s, M(4));
+          F0[c] = P::fma3(M(3), r, M(1));
+          F1[c] = P::fma3(M(6), r, M(5));
+        }
         typename P::A q = P::mul0(M(4), r);
         P::mac(q, M(5), s);
         P::mac(q, M(6), rs);
         J2[c] = P::add(M(2), P::fin(q));
       }
-      k00[0] = dot3<P>(E0, E0); k00[1] = P::twice(dot3<P>(E0, E1)); k00[2] = dot3<P>(E1, E1);
-      k11[0] = dot3<P>(F0, F0); k11[1] = P::twice(dot3<P>(F0, F1)); k11[2] = dot3<P>(F1, F1);
+      if constexpr (!AX) {
+        k00[0] = dot3<P>(E0, E0); k00[1] = P::twice(dot3<P>(E0, E1)); k00[2] = dot3<P>(E1, E1);
+        k11[0] = dot3<P>(F0, F0); k11[1] = P::twice(dot3<P>(F0, F1)); k11[2] = dot3<P>(F1, F1);
+      }
       // K = J^T J as polynomials in t
       k01[0] = dot3<P>(E0, F0); k01[1] = P::add(dot3<P>(E0, F1), dot3<P>(E1, F0)); k01[2] = dot3<P>(E1, F1);
       k02[0] = dot3<P>(E0, J2); k02[1] = dot3<P>(E1, J2);
@@ -434,6 +483,10 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   S *b0 = xs + EPB * ES;       // x0, later r
   S *b1 = b0 + EPB * ES;       // x1, later s
   __shared__ S sgeo[EPB][GW > 0 ? GW : 1];
+  // trilinear kinds: the per-element axis terms of the geometry (axis_terms)
+  constexpr bool AXS = kShareAxis<P, N1, KIND>;
+  constexpr int AXW = Geometry<P, N1, KIND>::kAxisWords;
+  __shared__ S sax[AXS ? EPB : 1][AXS ? 2 * N1 * AXW : 1];
 
   const int tid = threadIdx.x;
   const int z = tid / Sh::F, q = tid % Sh::F;
@@ -480,6 +533,11 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
   }
   __syncthreads();
+  if constexpr (AXS) {
+    // threads q < 2 N1 of each element: the N1 r-axis and N1 s-axis terms,
+    // read by every thread's geometry prologue after the next barriers
+    if (live && q < 2 * N1) Geometry<P, N1, KIND>::axis_terms(sgeo[z], cx, q / N1, q % N1, &sax[z][q * AXW]);
+  }
 
   S *x_e = xs + z * ES, *r_e = b0 + z * ES, *s_e = b1 + z * ES;
   // Six fiber products in two rolled phase loops (one code copy of the fiber
@@ -513,8 +571,8 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     // thread (i, j) = (qa, qb): geometry and G x along its own t-fiber
     const int i = qa, j = qb;
     Geometry<P, N1, KIND> gm;
-    gm.prologue(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
-                (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
+    gm.template prologue<AXS>(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+                              (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr, sax[AXS ? z : 0]);
     auto node = [&](int k) {
       const int sidx = ft + k * str_t;
       const V xv[3] = {P::ld(r_e + sidx), P::ld(s_e + sidx), P::ld(x_e + sidx)};
@@ -588,8 +646,9 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     {
       const int i = qa, j = qb;
       Geometry<P, N1, KIND> gm;
-      gm.prologue(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
-                  (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr);
+      gm.template prologue<AXS>(sgeo[z], cx, cw, i, j,
+                                (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+                                (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr, sax[AXS ? z : 0]);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
@@ -686,10 +745,18 @@ cudaError_t launch_ax_em(const AxArgs &a) {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     }
+    static int static_smem = -1;
+    if (static_smem < 0) {
+      cudaFuncAttributes fa;
+      static_smem = cudaFuncGetAttributes(&fa, ax_fiber_kernel<P, N1, KIND, EM>) == cudaSuccess ? (int)fa.sharedSizeBytes : 4096;
+    }
     const int warps = (Sh::threads + 31) / 32;
     int ctas = (P::kTargetWarpsPerSM + warps / 2) / warps;
     if (ctas < 1) ctas = 1;
-    const size_t cap = sm_smem > 0 ? (size_t)sm_smem / ctas - 2048 : 0;
+    // per CTA: dynamic + static shared memory + the 1 KB the hardware
+    // reserves, with 1 KB to spare (with none the driver chose a smaller
+    // shared-memory carveout and only ctas - 1 CTAs fitted: measured)
+    const size_t cap = sm_smem > 0 ? (size_t)sm_smem / ctas - (size_t)static_smem - 2048 : 0;
     if (cap > smem && cap <= 200 * 1024) smem = cap;
   }
   // per instantiation; static shared memory counts against the same 48 KB
