@@ -208,10 +208,13 @@ constexpr bool kFillWarps =
 // Minimum resident CTAs for the register budget (0: no bound): the
 // double-word kernels at N1 = 16 (256-thread CTAs) are held to 128 registers
 // so that two CTAs fit per SM (unbounded they take about 147 and run one CTA
-// per SM, 5-30% slower).  Elsewhere no bound is given: even an explicit 1
-// changes the register allocation for the worse.
+// per SM, 5-30% slower); the double-word trilinear kernel at N1 = 12
+// (288-thread CTAs) likewise to two CTAs (96 registers and some spills
+// instead of 119 registers and one CTA: 33% faster; the partial kind
+// measured 5% slower so and keeps its allocation).  Elsewhere no bound is
+// given: even an explicit 1 changes the register allocation for the worse.
 template <class P, int N1, int KIND>
-constexpr int kMinCtas = (P::kRoll && N1 == 16) ? 2 : 0;
+constexpr int kMinCtas = (P::kRoll && (N1 == 16 || (N1 == 12 && KIND == AX_GEOM_TRILINEAR))) ? 2 : 0;
 
 // Trilinear kinds: whether an element's first 2 N1 threads compute the axis
 // terms of the geometry (Geometry::axis_terms) for all its threads.  Measured
