@@ -40,11 +40,11 @@ double pipe_ops_per_node(int N1, int kind, int prec) {
   // the K01, K02, K12, K22 coefficients and, for det J, 6 two-term
   // determinants and 4 dot products; all amortised over the N1 nodes of the
   // thread's fiber.  Where the kernel shares the axis terms (native FP64;
-  // double-word up to N1 = 5) the first 2 N1 threads of an element compute
+  // double-word up to N1 = 6) the first 2 N1 threads of an element compute
   // them once, counted as the whole warps that run them (an element's share
   // of a warp below 32 threads per element).
   const bool share = (kind == AX_GEOM_TRILINEAR || kind == AX_GEOM_TRILINEAR_PARTIAL) &&
-                     (dwp ? N1 <= 5 : prec == AX_FP64);
+                     (dwp ? N1 <= 6 : prec == AX_FP64);
   const double twice = dwp ? 2.0 : 1.0;
   const double axis_set = 6.0 * fma + 3.0 * dot3 + twice;  // one r- or s-axis set
   const int F = N1 * N1;

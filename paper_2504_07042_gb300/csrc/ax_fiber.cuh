@@ -218,12 +218,13 @@ constexpr int kMinCtas = (P::kRoll && (N1 == 16 || (N1 == 12 && KIND == AX_GEOM_
 
 // Trilinear kinds: whether an element's first 2 N1 threads compute the axis
 // terms of the geometry (Geometry::axis_terms) for all its threads.  Measured
-// on GB300: native FP64 3% faster (N = 7), double-word 7% faster at N = 3 but
-// 1-4% slower at N = 7 (where the prologue is amortised over more nodes),
-// FP32 1-3% slower; so native FP64 at every order, double-word up to N1 = 5.
+// on GB300: native FP64 3% faster (N = 7), double-word 7% faster at N = 3 and
+// 3% at N = 5 but 1-4% slower at N = 7 (where the prologue is amortised over
+// more nodes), FP32 1-3% slower; so native FP64 at every order, double-word
+// up to N1 = 6.
 template <class P, int N1, int KIND>
 constexpr bool kShareAxis = (KIND == AX_GEOM_TRILINEAR || KIND == AX_GEOM_TRILINEAR_PARTIAL) &&
-                            (P::kRoll ? N1 <= 5 : sizeof(typename P::V) == 8);
+                            (P::kRoll ? N1 <= 6 : sizeof(typename P::V) == 8);
 
 template <int N1, int EM = 1, bool FILL = false>
 struct Shape {
