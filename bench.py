@@ -45,7 +45,7 @@ FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (meas
 # the same kernel (profiles/ax_dw_trilinear_n7_e32768_full.md), scaled by
 # elements to the 64x64x32 workload (traffic grows with the element count);
 # valid while the kernel's sources hash to "src".
-TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.567552e6 + 90.682112e6), "src": "4428f379afe6e482"}}
+TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.567552e6 + 90.682112e6), "src": "c79c362ef5553bda"}}
 
 
 # the sources that define the headline kernel (double-word AxLocal, N = 7)

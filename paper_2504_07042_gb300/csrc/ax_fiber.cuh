@@ -514,11 +514,12 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   // double-word data at N1 = 16 are read coalesced (load_rows): measured on
   // GB300 4-16% faster than one row per thread for float32 at N = 3 and 7,
   // 3-10% for double-word at N = 15.  Elsewhere one i-row of N1 values per
-  // thread: the coalesced form measured 10% slower for float32 N = 5 (the
-  // row and column of each value cost a division there), 2% slower for
-  // double-word N = 7 and, through a register increase that halves the
-  // resident CTAs, 23% slower for float32 N = 15 (the compiler raises the
-  // register count at every N1 >= 11 of the float32 kernels with it).
+  // thread: the coalesced form measured 10% slower for float32 N = 5 and 29%
+  // for double-word N = 5 (the row and column of each value cost a division
+  // there), 2% slower for double-word N = 3 and 7 and, through a register
+  // increase that halves the resident CTAs, 23% slower for float32 N = 15
+  // (the compiler raises the register count at every N1 >= 11 of the float32
+  // kernels with it).
   {
     using IO = typename P::IO;
     const IO *src = X + e0 * n3;
