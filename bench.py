@@ -206,6 +206,19 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def cpu_oracle_rate_single_thread(seconds=3.0, N=HEADLINE_N):
+    """cpu_oracle_rate on one host thread (the oracle's OpenMP team set to 1,
+    then restored); returns (GDOF/s, sample)."""
+    from oracle import oracle
+    n = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        rate, _, sample = cpu_oracle_rate(seconds, N)
+    finally:
+        oracle.set_num_threads(n)
+    return rate, sample
+
+
 def cpu_oracle_rate(seconds=10.0, N=HEADLINE_N):
     """FP64 oracle AxLocal (Eq. 9 + Eq. 7 + Algorithm 1, OpenMP over elements)
     on a bounded sample of the workload mesh; returns (GDOF/s, cores, sample)."""
@@ -350,7 +363,9 @@ def run(args):
             "roofline": roof_line, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
     if rank == 0:
         rate, cores, sample = cpu_oracle_rate()
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        rate1, sample1 = cpu_oracle_rate_single_thread()
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                                "single_thread": {"value": rate1, "unit": UNIT, "sample": sample1}}
         if pcg is not None:
             line["pcg"] = pcg
         if batch is not None:
