@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -34,8 +36,9 @@ UNIT = "GDOF/s"
 HEADLINE_N = 7
 HEADLINE_KIND = "trilinear"
 HEADLINE_PREC = "f64dw"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 SMSPs x 32)
+SM_COUNT = 152  # GB300; run() reads the live count from the device
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 SMSPs x 32): the unit-count peak
+FP32_FFMA_MEASURED_PER_SM_CLK = 116  # FFMA per SM per clock reached by a dependent-chain probe (91% of 128)
 FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (measured 1.19 TFLOP/s)
 
 # dram bytes per launch from committed ncu captures, valid while the kernel
@@ -164,21 +167,21 @@ def whole_job_value(world, dofs_per_rank, ms_max):
     return world * dofs_per_rank / (ms_max * 1e-3) / 1e9
 
 
-def _pipe_peak(info, sm_mhz):
+def _pipe_peak(info, sm_mhz, sms=SM_COUNT):
     clk = (sm_mhz or 1980.0) * 1e6
     if info["pipe"] == 0:
-        return FP64_OPS_PER_SM_CLK * SM_COUNT * clk, "FP64 pipe"
-    return FP32_LANES_PER_SM * SM_COUNT * clk, "FP32 pipe"
+        return FP64_OPS_PER_SM_CLK * sms * clk, "FP64 pipe"
+    return FP32_LANES_PER_SM * sms * clk, "FP32 pipe"
 
 
-def _roofline(info, ms, sm_mhz, hbm_gbs):
+def _roofline(info, ms, sm_mhz, hbm_gbs, sms=SM_COUNT):
     """Time-based roofline of Sec. 3.4: T_mem = bytes / measured HBM bandwidth,
     T_cmp = pipe instructions / pipe peak; frac = max(T_cmp, T_mem) / T_meas."""
     E = info["E"]
     t = ms * 1e-3
     bytes_ = info["bytes_per_element"] * E
     ops = info["pipe_ops_per_element"] * E
-    pipe_peak, pipe_name = _pipe_peak(info, sm_mhz)
+    pipe_peak, pipe_name = _pipe_peak(info, sm_mhz, sms)
     t_mem = bytes_ / (hbm_gbs * 1e9)
     t_cmp = ops / pipe_peak
     F = info["flops_ax_per_element"] * E
@@ -194,6 +197,9 @@ def _roofline(info, ms, sm_mhz, hbm_gbs):
     else:
         r.update({"bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm_gbs, "unit": "GB/s"})
     r["frac"] = r["achieved"] / r["peak"]
+    if r["bound"] == "alu" and info["pipe"] != 0:
+        # the same work against the FFMA rate a probe kernel actually reaches
+        r["frac_vs_measured_ffma"] = r["frac"] * FP32_LANES_PER_SM / FP32_FFMA_MEASURED_PER_SM_CLK
     return r
 
 
@@ -245,6 +251,35 @@ def cpu_oracle_rate(seconds=10.0, N=HEADLINE_N):
             "%d pass(es) over the first %d of %d elements (%.1f s)" % (reps, m, V.shape[0], dt))
 
 
+def cpu_oracle_sweep(seconds=1.5):
+    """The FP64 oracle AxLocal on every order-sweep mesh (N in {3,5,7,9,11,15},
+    perturbed trilinear box and parallelepiped box), all host threads, each on
+    a bounded sample of about `seconds` of CPU work; GDOF/s per case."""
+    from oracle import oracle
+    from paper_2504_07042_gb300 import inputs
+    out = []
+    for N in (3, 5, 7, 9, 11, 15):
+        ex, ey, ez = inputs.sweep_box(N)
+        n3 = (N + 1) ** 3
+        for mesh in ("trilinear", "parallelepiped"):
+            if mesh == "parallelepiped":
+                V = inputs.parallelepiped_vertices(ex, ey, ez)
+            else:
+                V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+            m = max(64, min(V.shape[0], int(2 ** 21 // n3)))
+            X = inputs.element_vectors(m, N, seed=1)
+            reps, t = 0, time.perf_counter()
+            while True:
+                oracle.axlocal_vertices(V[:m], X, N)
+                reps += 1
+                dt = time.perf_counter() - t
+                if dt >= seconds:
+                    break
+            out.append({"N": N, "mesh": mesh, "gdofs": reps * m * n3 / dt / 1e9, "elements_in_sample": m,
+                        "passes": reps, "seconds": dt, "threads": oracle.num_threads()})
+    return out
+
+
 def headline_config(world):
     """The workload the bench line measures (both arms report it)."""
     return {"workload": "order sweep at N=7: perturbed trilinear box 64x64x32 = 131072 elements, "
@@ -285,6 +320,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _detail_path(args):
+    if args.detail:
+        return args.detail
+    return os.path.join(ROOT, "gpurun_out", "bench_detail.json")
+
+
+def _write_detail(path, detail):
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(detail, f, indent=1)
+        return path
+    except OSError as e:
+        sys.stderr.write("bench: could not write %s: %s\n" % (path, e))
+        return None
+
+
 def run(args):
     import torch
     world, rank, local = _dist()
@@ -293,6 +345,7 @@ def run(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     from paper_2504_07042_gb300 import ax
     peaks, peak_src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -319,17 +372,20 @@ def run(args):
     ms = reduce_max_ms(torch, t0.elapsed_time(t1) / args.steps, dev)
     clocks = ck.summary()
     value = whole_job_value(world, E * n3, ms)
-    roof = _roofline(info, ms, clocks.get("sm_mhz"), hbm)
+    roof = _roofline(info, ms, clocks.get("sm_mhz"), hbm, sms)
     src = _src_hash()
     kname = "ax_fiber_kernel<DW, 8, %d, 1>" % info["kind"]
     traffic = TRAFFIC.get(kname)
+    alu = roof["bound"] == "alu"
     roof_line = {"bound": roof["bound"], "achieved": roof["achieved"], "peak": roof["peak"], "unit": roof["unit"],
                  "frac": roof["frac"], "traffic": traffic["bytes"] if traffic and traffic["src"] == src else None,
-                 "kernel": kname, "peak_source": ("%s (%d lanes/SM x %d SMs x median SM clock)"
-                                                  % (roof["pipe"], FP32_LANES_PER_SM, SM_COUNT)
-                                                  if roof["bound"] == "alu" else "hbm_gbs of MEASURED_PEAKS.json (%s)" % peak_src),
-                 "time_based": {k: roof[k] for k in ("t_mem_ms", "t_cmp_ms", "t_meas_ms", "P_eff_gflops",
-                                                     "R_eff_gflops", "frac_time_roofline", "hbm_gbs_achieved")}}
+                 "kernel": kname,
+                 "peak_source": ("%s: %d lanes/SM x %d SMs x median SM clock (unit counts)"
+                                 % (roof["pipe"], FP32_LANES_PER_SM, sms) if alu
+                                 else "hbm_gbs of MEASURED_PEAKS.json (%s)" % peak_src)}
+    if "frac_vs_measured_ffma" in roof:
+        roof_line["frac_vs_measured_ffma"] = roof["frac_vs_measured_ffma"]
+    roof_line["hbm_frac_of_measured"] = roof["hbm_gbs_achieved"] / hbm
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     Xh = torch.from_numpy(X.cpu().numpy()).pin_memory()
@@ -345,16 +401,21 @@ def run(args):
     e2e = {"value": world * E * n3 / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
     del Xh, Yh
+    op.ax_destroy()
+    del X, Y
+    torch.cuda.empty_cache()
 
-    sweep = None
-    pcg = None
-    batch = None
-    learned_pc = None
+    detail = {"headline": {"roofline_time_based": {k: roof[k] for k in (
+        "t_mem_ms", "t_cmp_ms", "t_meas_ms", "P_eff_gflops", "R_eff_gflops", "frac_time_roofline",
+        "hbm_gbs_achieved")}, "sms": sms, "src_hash": src}}
     if not args.no_sweep and rank == 0:
-        sweep = run_sweep(ax, torch, dev, hbm, clocks.get("sm_mhz"))
-        pcg = run_pcg(ax, torch, dev)
-        batch = run_batch(ax, torch, dev)
-        learned_pc = run_learned(ax, torch, dev)
+        for name, f in (("sweep", lambda: run_sweep(ax, torch, dev, hbm, clocks.get("sm_mhz"), sms)),
+                        ("pcg", lambda: run_pcg(ax, torch, dev)),
+                        ("batch", lambda: run_batch(ax, torch, dev)),
+                        ("learned", lambda: run_learned(ax, torch, dev))):
+            t = time.perf_counter()
+            detail[name] = f()
+            sys.stderr.write("bench: %s section done in %.1f s\n" % (name, time.perf_counter() - t))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -365,26 +426,47 @@ def run(args):
         rate, cores, sample = cpu_oracle_rate()
         rate1, sample1 = cpu_oracle_rate_single_thread()
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-                                "single_thread": {"value": rate1, "unit": UNIT, "sample": sample1}}
-        if pcg is not None:
-            line["pcg"] = pcg
-        if batch is not None:
-            line["batch"] = batch
-        if learned_pc is not None:
-            line["learned"] = learned_pc
-        if sweep is not None:
-            line["sweep"] = sweep
-        print(json.dumps(line), flush=True)
+                                "single_thread_value": rate1}
+        detail["cpu_baseline_single_thread"] = {"value": rate1, "unit": UNIT, "sample": sample1}
+        if not args.no_sweep:
+            detail["cpu_oracle_sweep"] = cpu_oracle_sweep()
+        line["detail"] = os.path.relpath(_write_detail(_detail_path(args), detail) or "", ROOT)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def cpu_oracle_pcg(N=7, n=16):
+    """CPU-baseline leg for the solver: the FP64 oracle's Jacobi-PCG on the
+    16^3 N = 7 Poisson problem to 1e-10 on the host cores, with its own
+    factors (Eq. 7), nodal coordinates, mass and gather.  Returns its solution
+    (the reference for the GPU solvers' errors) and its timing."""
+    from oracle import oracle
+    from paper_2504_07042_gb300 import inputs
+    V = inputs.box_vertices(n, n, n, perturb=0.1, seed=0)
+    gid, ng = inputs.box_global_ids(n, n, n, N)
+    mask = inputs.box_boundary_mask(n, n, n, N)
+    G, _ = oracle.factors(V, N)
+    P = oracle.nodal_coords(V, N)
+    f = 3 * np.pi ** 2 * np.sin(np.pi * P[:, 0]) * np.sin(np.pi * P[:, 1]) * np.sin(np.pi * P[:, 2])
+    b = oracle.gather(G[:, 6, :] * f, gid, ng)
+    t = time.perf_counter()
+    x, it, rr, ok = oracle.pcg(G, gid, ng, mask, b, N, rtol=1e-10, maxit=20000)
+    dt = time.perf_counter() - t
+    return x, {"seconds": dt, "iterations": it, "relres": rr, "converged": bool(ok), "rtol": 1e-10,
+               "threads": oracle.num_threads(), "what": "FP64 CPU oracle Jacobi-PCG (Eq. 1; Algorithm 1 with "
+                                                        "Eq. 7 factors), right-hand side built by the oracle"}
 
 
 def run_pcg(ax, torch, dev):
     """Poisson -lap u = 3 pi^2 u, u = sin(pi x) sin(pi y) sin(pi z), homogeneous
     Dirichlet, 16^3 perturbed trilinear elements at N = 7: wall time to 1e-8
     relative residual for FP64-accurate Jacobi-PCG (double-word AxLocal) and
-    for the mixed-precision solver (FP64 refinement, float32 inner PCG)."""
+    for the mixed-precision solver (FP64 refinement around a float32 inner PCG
+    whose AxLocal contracts in FP32, TF32, BF16 or FP16), and each solution's
+    error against the FP64 oracle's own PCG solve of the same problem (its
+    right-hand side built by the oracle), which is timed on the host cores."""
     from paper_2504_07042_gb300 import inputs
     N, n = 7, 16
     V = inputs.box_vertices(n, n, n, perturb=0.1, seed=0)
@@ -393,17 +475,25 @@ def run_pcg(ax, torch, dev):
     Vd = torch.from_numpy(V).to(dev)
     hi = ax.Ax(Vd, N, "trilinear", "f64dw")
     hi.gs_setup(torch.from_numpy(gid).to(dev), ng, torch.from_numpy(mask).to(dev))
-    lo = ax.Ax(Vd, N, "trilinear", "fp32")
     XYZ = torch.empty((V.shape[0], 3, (N + 1) ** 3), dtype=torch.float64, device=dev)
     hi.ax_node_coords(XYZ)
     u = torch.sin(torch.pi * XYZ[:, 0]) * torch.sin(torch.pi * XYZ[:, 1]) * torch.sin(torch.pi * XYZ[:, 2])
     b = hi.gs_gather(hi.ax_mass(3 * torch.pi ** 2 * u, torch.empty_like(u)), torch.empty(ng, dtype=torch.float64, device=dev))
     ug = torch.zeros(ng, dtype=torch.float64, device=dev)
     ug[torch.from_numpy(gid.reshape(-1)).to(dev)] = u.reshape(-1)
-    out = {"workload": "16^3 perturbed trilinear elements, N=7, %d global nodes, rtol 1e-8" % ng}
-    for name, fn in (("fp64_jacobi_pcg", lambda x: hi.pcg_solve(b, x, rtol=1e-8, maxit=20000, precond=1)),
-                     ("mixed_fp64_refinement_fp32_inner", lambda x: hi.pcg_solve_mixed(lo, b, x, rtol=1e-8,
-                                                                                      inner_rtol=1e-3))):
+
+    x_orc, orc_pcg = cpu_oracle_pcg()
+    x_orc_d = torch.from_numpy(x_orc).to(dev)
+    nrm = float(x_orc_d.abs().max())
+    out = {"workload": "16^3 perturbed trilinear elements, N=7, %d global nodes, rtol 1e-8" % ng,
+           "oracle_pcg": orc_pcg}
+    los = {p: ax.Ax(Vd, N, "trilinear", p) for p in ("fp32", "tf32", "bf16", "fp16")}
+    runs = [("fp64_jacobi_pcg", lambda x: hi.pcg_solve(b, x, rtol=1e-8, maxit=20000, precond=1))]
+    for p, inner_rtol in (("fp32", 1e-3), ("tf32", 1e-2), ("bf16", 1e-2), ("fp16", 1e-2)):
+        runs.append(("mixed_fp64_refinement_%s_inner" % p,
+                     lambda x, lo=los[p], r=inner_rtol: hi.pcg_solve_mixed(lo, b, x, rtol=1e-8, inner_rtol=r,
+                                                                           max_outer=100)))
+    for name, fn in runs:
         x = torch.zeros(ng, dtype=torch.float64, device=dev)
         fn(x)  # warm-up (allocations, module loading)
         x.zero_()
@@ -412,10 +502,20 @@ def run_pcg(ax, torch, dev):
         res = fn(x)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
-        out[name] = {"seconds": dt, "result": list(res), "max_error_vs_exact": float((x - ug).abs().max())}
+        out[name] = {"seconds": dt, "result": list(res), "max_error_vs_exact": float((x - ug).abs().max()),
+                     "rel_error_vs_oracle_solve": float((x - x_orc_d).abs().max()) / nrm}
+        # the same solver to 1e-10 (the refinement's stated tolerance): error against the oracle solve
+        x.zero_()
+        if name == "fp64_jacobi_pcg":
+            hi.pcg_solve(b, x, rtol=1e-10, maxit=20000, precond=1)
+        else:
+            lo = los[name.split("_")[3]]
+            hi.pcg_solve_mixed(lo, b, x, rtol=1e-10, inner_rtol=1e-3 if lo is los["fp32"] else 1e-2, max_outer=100)
+        out[name]["rel_error_vs_oracle_solve_at_1e-10"] = float((x - x_orc_d).abs().max()) / nrm
     out["speedup_mixed_over_fp64"] = out["fp64_jacobi_pcg"]["seconds"] / out["mixed_fp64_refinement_fp32_inner"]["seconds"]
     hi.ax_destroy()
-    lo.ax_destroy()
+    for lo in los.values():
+        lo.ax_destroy()
     return out
 
 
@@ -558,7 +658,7 @@ def run_learned(ax, torch, dev):
     return out
 
 
-def run_sweep(ax, torch, dev, hbm, sm_mhz):
+def run_sweep(ax, torch, dev, hbm, sm_mhz, sms=SM_COUNT):
     """Per-N GDOF/s and roofline fraction, recompute vs stored, per precision."""
     out = []
     stream = torch.cuda.current_stream()
@@ -571,10 +671,11 @@ def run_sweep(ax, torch, dev, hbm, sm_mhz):
                     op, X, Y, _ = _build_case(ax, torch, dev, N, kind, prec, mesh)
                     info = op.ax_query()
                     ms = _time_launches(torch, lambda: op.ax_local(X, Y, stream), 5, 2, stream)
-                    roof = _roofline(info, ms, sm_mhz, hbm)
+                    roof = _roofline(info, ms, sm_mhz, hbm, sms)
                     out.append({"N": N, "mesh": mesh, "kind": kind, "prec": prec, "E": op.E,
                                 "gdofs": op.E * op.n3 / (ms * 1e-3) / 1e9, "ms": ms, "bound": roof["bound"],
-                                "frac": roof["frac"], "P_eff_gflops": roof["P_eff_gflops"],
+                                "frac": roof["frac"], "frac_vs_measured_ffma": roof.get("frac_vs_measured_ffma"),
+                                "P_eff_gflops": roof["P_eff_gflops"],
                                 "hbm_gbs": roof["hbm_gbs_achieved"]})
                     op.ax_destroy()
                     del X, Y
@@ -589,6 +690,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--detail", default=None, help="side file for the sweep and solver sections "
+                    "(default gpurun_out/bench_detail.json)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

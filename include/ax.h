@@ -112,11 +112,13 @@ ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *strea
  *   ax_local).  Copies X in, runs the same AxLocal kernel, copies Y out,
  *   synchronises the stream.
  * It calls no cudaMalloc/cudaFree: X and Y are staged through one file-scope
- * device array of 32 MiB (16 MiB per vector), which every GPU that loads the
- * library holds until the process exits.  E * (N+1)^3 * word size above
- * 16 MiB returns AX_EINVAL (use ax_local_host or ax_local instead).
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * device array of 32 MiB (16 MiB per vector).  ax_setup looks up the array's
+ * device address with the context's device current; that lookup loads the
+ * library module holding the array, so the array is committed during
+ * ax_setup on every GPU where a context is set up, and stays until the
+ * process exits.  The entry point itself does no look-up, no module load and
+ * no allocation.  E * (N+1)^3 * word size above 16 MiB returns AX_EINVAL
+ * (use ax_local_host or ax_local instead).
  * All calls share the array and it keeps the last call's contents: calls
  * that overlap on the GPU (several host threads or streams at once) race,
  * so callers must serialise them. */
@@ -167,8 +169,10 @@ ax_status ax_diag(ax_ctx *c, void *diag_local, void *stream);
  * context's AxLocal kernel.
  *   b_global, x_global: device [n_global] (float64 for AX_FP64/AX_F64DW,
  *   float32 otherwise); x_global is the initial guess and receives the
- *   solution.  precond: 0 = none, 1 = Jacobi (assembled diagonal).
- *   Stops when ||r||_2 <= rtol ||b||_2 or after maxit iterations
+ *   solution.  precond: 0 = none, 1 = Jacobi (assembled diagonal); 2 (the
+ *   learned preconditioner) returns AX_EINVAL: it needs a network handle,
+ *   so it has its own entry point, pcg_solve_learned(ctx, mlp, ...).
+ *   Other values return AX_EUNSUPPORTED.  Stops when ||r||_2 <= rtol ||b||_2 or after maxit iterations
  *   (AX_ENOTCONV).  *iters and *relres (host) report the outcome.
  * One iteration is four kernels (direction + scatter, AxLocal, gather + p.w
  * with alpha, update + r.z, r.r with the convergence test and beta); every

@@ -28,11 +28,14 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (gcc, -O2, OpenMP)."""
+    """Compile oracle.c into _build/liboracle.so (gcc, -O3, OpenMP).  No
+    -march=native: the same source builds on x86-64 and Arm hosts, and the
+    compiler may not reassociate (no -ffast-math), so -O3 keeps the order of
+    every floating-point operation as written."""
     os.makedirs(_LIB_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 

@@ -169,12 +169,33 @@ class Ax:
         _check(_lib.ax_local(self.ctx, _ptr(X), _ptr(Y), _stream(stream)), self.ctx)
         return Y
 
+    def _host_io(self, name, X_host, Y_host):
+        """Host buffers for the host entry points: C-contiguous, the context's
+        value type, at least E * (N+1)^3 values each (the C side copies that
+        many bytes from X and to Y)."""
+        import numpy as np
+        import torch
+        want = self.E * self.n3
+        for tag, a in (("X_host", X_host), ("Y_host", Y_host)):
+            if isinstance(a, torch.Tensor):
+                ok = a.device.type == "cpu" and a.is_contiguous() and a.dtype == self.dtype and a.numel() >= want
+            elif isinstance(a, np.ndarray):
+                npdt = np.float64 if self.dtype == torch.float64 else np.float32
+                ok = a.flags["C_CONTIGUOUS"] and a.dtype == npdt and a.size >= want
+            else:
+                ok = False
+            if not ok:
+                raise TypeError("%s: %s must be a C-contiguous host array of %s with at least %d values"
+                                % (name, tag, self.dtype, want))
+
     def ax_local_host(self, X_host, Y_host, stream=None):
+        self._host_io("ax_local_host", X_host, Y_host)
         _check(_lib.ax_local_host(self.ctx, _ptr(X_host), _ptr(Y_host), _stream(stream)), self.ctx)
         return Y_host
 
     def ax_local_host_static(self, X_host, Y_host, stream=None):
         """ax_local_host without device allocation (fixed 16 MiB per vector)."""
+        self._host_io("ax_local_host_static", X_host, Y_host)
         _check(_lib.ax_local_host_static(self.ctx, _ptr(X_host), _ptr(Y_host), _stream(stream)), self.ctx)
         return Y_host
 

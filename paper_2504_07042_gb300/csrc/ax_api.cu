@@ -13,7 +13,12 @@
 struct ax_ctx {
   ax::Ctx c;
   double *vtx = nullptr;  // copy of the caller's vertices (node coordinates, exports)
+  void *static_stage = nullptr;  // device address of the file-scope staging array (ax_local_host_static)
 };
+
+namespace {
+cudaError_t static_stage_address(void **out);  // defined beside the array, at the end of this file
+}
 
 namespace {
 
@@ -184,6 +189,10 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
     if (e == cudaSuccess && (prec == AX_TF32 || prec == AX_BF16 || prec == AX_FP16))
       e = ax::upload_tables_fp32(c->c.device);
   }
+  // The device address of ax_local_host_static's staging array, looked up
+  // here with the context's device current: the lookup loads this file's
+  // module (committing the array) during set-up, never inside that call.
+  if (e == cudaSuccess) e = static_stage_address(&c->static_stage);
   if (e != cudaSuccess) {
     ax_status st = cuda_fail(nullptr, e, "ax_setup: table upload");
     delete c;
@@ -497,6 +506,9 @@ ax_status pcg_solve(ax_ctx *c, const void *b_global, void *x_global, double rtol
   if (!c) return fail(nullptr, AX_EINVAL, "pcg_solve: context is NULL");
   if (!has_gs(c)) return fail(c, AX_EINVAL, "pcg_solve: call gs_setup first");
   if (!iters || !relres) return fail(c, AX_EINVAL, "pcg_solve: iters or relres is NULL");
+  if (precond == 2)
+    return fail(c, AX_EINVAL,
+                "pcg_solve: precond 2 (learned) needs a network handle: call pcg_solve_learned(ctx, mlp, ...)");
   if (precond != 0 && precond != 1) return fail(c, AX_EUNSUPPORTED, "pcg_solve: precond must be 0 (none) or 1 (Jacobi)");
   if (!(rtol >= 0.0) || maxit < 0) return fail(c, AX_EINVAL, "pcg_solve: bad rtol or maxit");
   if (c->c.gs.n_global && (!b_global || !x_global)) return fail(c, AX_EINVAL, "pcg_solve: NULL vector");
@@ -581,8 +593,12 @@ void ax_destroy(ax_ctx *c) {
 // cudaMalloc/cudaFree synchronise the device in the middle of their work.
 // ax_local_host allocates its device staging buffers on first use, which
 // such callers cannot allow.  This entry point stages X and Y through one
-// file-scope device array instead, of a fixed size (kStaticStageBytes, held
-// on every GPU that loads the library until the process exits).
+// file-scope device array instead, of a fixed size (kStaticStageBytes).  The
+// array lives in this file's module: ax_setup looks up its device address
+// (which loads the module, and so commits the array, on that device), so
+// every GPU on which a context was set up holds it until the process exits,
+// and the entry point itself never triggers a module load.  The address is
+// kept in the context, which does not outlive a device reset.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -591,8 +607,10 @@ constexpr size_t kStaticStageHalf = kStaticStageBytes / 2;  // X half, Y half
 
 static __device__ __align__(256) unsigned char g_static_stage[kStaticStageBytes];
 
-std::mutex g_static_stage_mu;
-void *g_static_stage_ptr[64] = {nullptr};
+cudaError_t static_stage_address(void **out) {
+  *out = nullptr;
+  return cudaGetSymbolAddress(out, g_static_stage);
+}
 
 }  // namespace
 
@@ -610,20 +628,8 @@ extern "C" ax_status ax_local_host_static(ax_ctx *c, const void *X_host, void *Y
              bytes, kStaticStageHalf);
     return fail(c, AX_EINVAL, msg);
   }
-  const int dev = c->c.device;
-  if (dev < 0 || dev >= 64) return fail(c, AX_EINVAL, "ax_local_host_static: device ordinal above 63");
-  void *base = nullptr;
-  {
-    // once per device, with that device current: the device address of the array
-    std::lock_guard<std::mutex> lock(g_static_stage_mu);
-    if (!g_static_stage_ptr[dev]) {
-      void *p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_static_stage);
-      if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host_static: cudaGetSymbolAddress");
-      g_static_stage_ptr[dev] = p;
-    }
-    base = g_static_stage_ptr[dev];
-  }
+  void *base = c->static_stage;  // looked up by ax_setup on this context's device
+  if (!base) return fail(c, AX_EINVAL, "ax_local_host_static: staging array address unknown");
   void *xd = base;
   void *yd = (unsigned char *)base + kStaticStageHalf;
   cudaStream_t s = (cudaStream_t)stream;

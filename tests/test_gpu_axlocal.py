@@ -252,14 +252,19 @@ def test_error_statuses(ax):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "f64dw"])
-@pytest.mark.parametrize("kind", ["stored", "trilinear"])
+@pytest.mark.parametrize("kind", ["stored", "trilinear", "partial", "parallelepiped"])
 def test_full_size_sampled(ax, orc, kind, prec):
     # the order-7 sweep workload (64x64x32 = 131072 elements, 67.1M local nodes),
     # in the launch configuration the benchmark times; 256 sampled elements
-    # checked against the oracle element by element.
+    # checked against the oracle element by element.  The parallelepiped kind
+    # runs on the sweep's sheared parallelepiped box, the others on the
+    # perturbed trilinear box.
     N = 7
     ex, ey, ez = inputs.sweep_box(N)
-    V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    if kind == "parallelepiped":
+        V = inputs.parallelepiped_vertices(ex, ey, ez)
+    else:
+        V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
     E = V.shape[0]
     X = inputs.element_vectors(E, N, seed=1)
     Y = _run(ax, V, X, N, kind, prec)

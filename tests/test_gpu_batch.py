@@ -1,5 +1,7 @@
 """Batched AxLocal and batched independent PCG solves over meshes of uneven
-size and order, against the per-mesh paths of the C ABI."""
+size and order, against the FP64 oracle mesh by mesh (AxLocal by Eq. 9,
+Eq. 7 and Algorithm 1; PCG by the oracle's textbook Jacobi-PCG) and against
+the per-mesh paths of the C ABI."""
 import numpy as np
 import pytest
 
@@ -36,6 +38,35 @@ def _meshes():
 def _dev(meshes):
     return [(torch.from_numpy(V).to(DEV), N, torch.from_numpy(g).to(DEV), ng, torch.from_numpy(m).to(DEV))
             for V, N, g, ng, m in meshes]
+
+
+# parity tolerances of each precision (relative max-norm against the FP64 oracle)
+TOL = {"fp64": 1e-12, "f64dw": 1e-12, "fp32": 2e-5, "tf32": 4 * 2.0 ** -11, "fp16": 4 * 2.0 ** -11,
+       "bf16": 4 * 2.0 ** -8}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "f64dw", "tf32", "bf16", "fp16"])
+def test_batch_local_matches_oracle(ax, orc, prec):
+    meshes = _meshes()
+    bt = ax.AxBatch(_dev(meshes), "trilinear", prec)
+    Xh = np.random.default_rng(71).uniform(-1, 1, bt.n_local)
+    X = torch.from_numpy(Xh).to(DEV, bt.dtype)
+    Xh = X.double().cpu().numpy()  # the values the kernel sees
+    for tuned in (False, True):
+        if tuned:
+            bt.ax_batch_tune()
+        Y = torch.full_like(X, float("nan"))
+        bt.ax_batch_local(X, Y)
+        Yh = Y.double().cpu().numpy()
+        for m, (V, N, gid, ng, mask) in enumerate(meshes):
+            n3 = (N + 1) ** 3
+            lo = bt.local_offsets[m]
+            Xm = Xh[lo:lo + V.shape[0] * n3].reshape(V.shape[0], n3)
+            Yref, bad = orc.axlocal_vertices(V, Xm, N)
+            assert bad == 0
+            Ym = Yh[lo:lo + V.shape[0] * n3].reshape(V.shape[0], n3)
+            err = np.max(np.abs(Ym - Yref)) / np.max(np.abs(Yref))
+            assert err <= TOL[prec], (m, N, tuned, err)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64", "f64dw", "tf32", "bf16"])
@@ -85,3 +116,33 @@ def test_batch_pcg_graph_vs_per_mesh(ax, orc, prec, tol):
         d = float((x1[a:b] - x0[a:b]).abs().max()) / float(x0[a:b].abs().max())
         assert d <= tol, (m, d)
         assert abs(it1[m] - it0[m]) <= 2, (m, it1[m], it0[m])
+
+
+@pytest.mark.parametrize("prec,rtol,tol", [("fp32", 1e-5, 1e-4), ("fp64", 1e-10, 1e-8), ("f64dw", 1e-10, 1e-8)])
+def test_batch_pcg_matches_oracle(ax, orc, prec, rtol, tol):
+    # each mesh's solution against the oracle's Jacobi-PCG of the same mesh and
+    # right-hand side (built by the oracle), solved to 1e-13; the tolerance is
+    # what stopping at rtol leaves (the oracle itself, stopped at 1e-5 and
+    # 1e-10 on these meshes, is 1e-6 to 5e-6 and 1e-11 to 2e-11 away)
+    meshes = _meshes()
+    bt = ax.AxBatch(_dev(meshes), "trilinear", prec)
+    bvec = np.zeros(bt.n_global)
+    xref = []
+    for m, (V, N, gid, ng, mask) in enumerate(meshes):
+        G, _ = orc.factors(V, N)
+        XYZ = orc.nodal_coords(V, N)
+        f = 3 * np.pi ** 2 * np.sin(np.pi * XYZ[:, 0]) * np.sin(np.pi * XYZ[:, 1]) * np.sin(np.pi * XYZ[:, 2])
+        b = orc.gather(G[:, 6, :] * f + 0.1, gid, ng)
+        bvec[bt.global_offsets[m]:bt.global_offsets[m + 1]] = b
+        x, it, rr, ok = orc.pcg(G, gid, ng, mask, b, N, rtol=1e-13, maxit=5000)
+        assert ok
+        xref.append(x)
+    bd = torch.from_numpy(bvec).to(DEV, bt.dtype)
+    x = torch.zeros_like(bd)
+    it, rr, st = bt.ax_batch_pcg(bd, x, rtol=rtol, maxit=5000, graph=1)
+    assert st == ax.AX_OK and all(r <= rtol for r in rr)
+    xh = x.double().cpu().numpy()
+    for m in range(bt.B):
+        a, b = bt.global_offsets[m], bt.global_offsets[m + 1]
+        d = np.max(np.abs(xh[a:b] - xref[m])) / np.max(np.abs(xref[m]))
+        assert d <= tol, (m, d)

@@ -125,6 +125,12 @@ def test_pcg_statuses(ax, orc):
     x.zero_()
     it, rr, st = op.pcg_solve(torch.zeros_like(b), x, rtol=1e-10, maxit=10)
     assert st == ax.AX_OK and it == 0 and float(x.abs().max()) == 0.0
+    with pytest.raises(ax.AxError) as ei:  # the learned preconditioner has its own entry point
+        op.pcg_solve(b, x, rtol=1e-8, maxit=10, precond=2)
+    assert ei.value.status == ax.AX_EINVAL and "pcg_solve_learned" in str(ei.value)
+    with pytest.raises(ax.AxError) as ei:
+        op.pcg_solve(b, x, rtol=1e-8, maxit=10, precond=3)
+    assert ei.value.status == ax.AX_EUNSUPPORTED
     with pytest.raises(ax.AxError) as ei:
         op.gs_setup(torch.from_numpy(gid + ng).to(DEV), ng)
     assert ei.value.status == ax.AX_EINVAL

@@ -57,6 +57,36 @@ def _setup(ax, seed=3, M=256):
     return mlp, Xd, Td, _bf16(X[:, :I]), T.astype(np.float64), Pq
 
 
+U_BF16 = 2.0 ** -8  # unit roundoff of bfloat16 (8 significand bits)
+GELU_LIP = 1.13  # max |gelu'|: a bound on how much gelu magnifies an error in its argument
+
+
+def _rss(A, B):
+    """Entry (i, j): sqrt(sum_m (A[m, i] B[m, j])^2), the root-sum-square size
+    of the terms of (A^T B)[i, j].  Independent roundings of the terms leave
+    an error of about u times this, while a wrong index, sign or dropped term
+    moves the entry by about this much."""
+    return np.sqrt((A * A).T @ (B * B))
+
+
+def _scales(Pq, X, T):
+    """Per-entry error scales of the forward output and the six gradients,
+    propagated through the network in absolute values (a term's error scale
+    is the size of the terms it sums, plus what its inputs already carry)."""
+    W1, b1, W2, b2, W3, b3 = Pq
+    M, O = T.shape
+    Z1 = np.sqrt((X * X) @ (W1 * W1).T) + np.abs(b1)
+    H1 = GELU_LIP * Z1
+    Z2 = np.sqrt((H1 * H1) @ (W2 * W2).T) + np.abs(b2) + H1 @ np.abs(W2).T * U_BF16
+    H2 = GELU_LIP * Z2
+    Y = np.sqrt((H2 * H2) @ (W3 * W3).T) + np.abs(b3) + H2 @ np.abs(W3).T * U_BF16
+    dY = (Y + np.abs(T)) / (M * O)
+    dZ2 = (dY @ np.abs(W3)) * (GELU_LIP + Z2)
+    dZ1 = (dZ2 @ np.abs(W2)) * (GELU_LIP + Z1)
+    return Y, [_rss(dZ1, X), np.sqrt((dZ1 * dZ1).sum(0)), _rss(dZ2, H1), np.sqrt((dZ2 * dZ2).sum(0)),
+               _rss(dY, H2), np.sqrt((dY * dY).sum(0))]
+
+
 def test_forward_matches_oracle(ax):
     from oracle import mlp as om
 
@@ -66,6 +96,11 @@ def test_forward_matches_oracle(ax):
     Yref, _ = om.forward(Pq, Xq)
     err = np.max(np.abs(Y.cpu().numpy() - Yref)) / np.max(np.abs(Yref))
     assert err < 2e-2  # bf16 hidden activations: ~2^-9 relative per rounding
+    # element by element: every output within a few bf16 roundings of its own scale
+    Ys, _ = _scales(Pq, Xq, np.zeros_like(Yref))
+    ratio = np.abs(Y.cpu().numpy() - Yref) / (U_BF16 * Ys)
+    print("forward: max |err| / (u * scale) = %.3f" % ratio.max())
+    assert ratio.max() < 8.0
 
 
 def test_gradients_match_oracle(ax):
@@ -77,10 +112,16 @@ def test_gradients_match_oracle(ax):
     assert abs(loss - Lref) / Lref < 1e-2
     G = _split(g.astype(np.float64))
     G[0] = G[0][:, :I]
-    for name, a, b in zip(("dW1", "db1", "dW2", "db2", "dW3", "db3"), G, gref):
+    _, scales = _scales(Pq, Xq, T)
+    for name, a, b, sc in zip(("dW1", "db1", "dW2", "db2", "dW3", "db3"), G, gref, scales):
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         cos = float(np.sum(a * b) / (np.linalg.norm(a) * np.linalg.norm(b)))
         assert rel < 5e-2 and cos > 0.998, (name, rel, cos)
+        # element by element, against each entry's own error scale: a wrong row,
+        # column or sign moves an entry by about its scale, bf16 roundings by ~u of it
+        ratio = np.abs(a - b) / (U_BF16 * sc)
+        print("%s: max |err| / (u * scale) = %.3f at %s" % (name, ratio.max(), np.unravel_index(ratio.argmax(), ratio.shape)))
+        assert ratio.max() < 8.0, (name, ratio.max())
     # the padded input columns never receive gradient
     assert np.all(_split(g)[0][:, I:] == 0.0)
 

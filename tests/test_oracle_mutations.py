@@ -45,7 +45,7 @@ def test_planted_mistake_is_caught(name, tmp_path):
     mut = tmp_path / "oracle_mut.c"
     mut.write_text(src.replace(old, new))
     lib = tmp_path / "liboracle_mut.so"
-    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", str(lib), str(mut), "-lm"])
+    subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", str(lib), str(mut), "-lm"])
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] + PINS,
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)

@@ -5,10 +5,12 @@ allowed).  It stages X and Y through the library's fixed 32 MiB device array
 instead of allocating.
 
 Checked through the C ABI against ax_local_host (same kernel, allocated
-staging buffers) on two calls in a row with different inputs, within the
-float64 tolerance used by the other parity tests; sizes beyond the array are
-rejected before any GPU work.  This module is collected last, so a failing
-run that stops at the first failure has already run every other test.
+staging buffers) on two calls in a row with different inputs, within each
+precision's parity tolerance and, since both run the same kernel on the same
+data, bit for bit; after a warm-up call, a call leaves the device's free
+memory unchanged; sizes beyond the array are rejected before any GPU work.
+This module is collected last, so a failing run that stops at the first
+failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -30,7 +32,7 @@ def ax():
     return _ax
 
 
-@pytest.mark.parametrize("prec,tol", [("f64dw", 1e-12), ("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("f64dw", 1e-12), ("fp64", 1e-12), ("fp32", 2e-5), ("tf32", 4 * 2.0 ** -11)])
 def test_static_staging_matches_allocating_entry_point(ax, prec, tol):
     N = 7
     V = inputs.box_vertices(8, 8, 8, perturb=0.1, seed=0)  # 512 elements: 2 MiB per float64 vector
@@ -46,6 +48,23 @@ def test_static_staging_matches_allocating_entry_point(ax, prec, tol):
         assert np.isfinite(Y).all()
         err = np.max(np.abs(Y.astype(np.float64) - Y_ref)) / np.max(np.abs(Y_ref))
         assert err <= tol
+        assert np.array_equal(Y, Y_ref)
+    op.ax_destroy()
+
+
+def test_static_staging_allocates_nothing(ax):
+    N = 7
+    V = inputs.box_vertices(8, 8, 8, perturb=0.1, seed=0)
+    op = ax.Ax(torch.from_numpy(V).to("cuda:0"), N, "trilinear", "f64dw")
+    X = inputs.element_vectors(V.shape[0], N, seed=4)
+    Y = np.empty_like(X)
+    op.ax_local_host_static(X, Y)  # warm-up: kernel module and local-memory pools in place
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    op.ax_local_host_static(X, Y)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
     op.ax_destroy()
 
 
