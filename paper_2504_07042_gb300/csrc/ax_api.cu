@@ -234,6 +234,11 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
     } else if (kind == AX_GEOM_PARALLELEPIPED && hflags[1]) {
       snprintf(msg, sizeof msg, "ax_setup: %d elements are not parallelepipeds", hflags[1]);
       st = fail(nullptr, AX_ENOTPARALLELEPIPED, msg);
+    } else if (hflags[3]) {
+      snprintf(msg, sizeof msg,
+               "ax_setup: %d elements have an extent outside [2^-20, 2^24], the range the FP32-based "
+               "precisions handle at full accuracy (scale the mesh, or use AX_FP64)", hflags[3]);
+      st = fail(nullptr, AX_ERANGE, msg);
     } else if (hflags[2]) {
       snprintf(msg, sizeof msg, "ax_setup: %d geometry values above 1e30 (or not finite) for an FP32-based precision", hflags[2]);
       st = fail(nullptr, AX_ERANGE, msg);

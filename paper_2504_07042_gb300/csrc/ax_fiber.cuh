@@ -44,6 +44,7 @@ struct Native {
   using C = T;   // constant-table word
   using IO = T;  // X, Y in HBM
   static constexpr bool kRoll = false;  // short code: unroll the phase and k loops
+  static constexpr bool kScaleIO = false;  // native range: X and Y pass unscaled
   static constexpr int kTargetWarpsPerSM = 0;  // no cap
   static constexpr int kTiles = sizeof(T) == 4 ? 2 : 1;  // tile variants the autotuner may pick
   __device__ static __forceinline__ V ld(const S *p) { return *p; }
@@ -82,6 +83,10 @@ struct DW {
   using C = float2;
   using IO = double;
   static constexpr bool kRoll = true;  // long code: keep the phase and k loops rolled (instruction cache)
+  // float64 X has float64's exponent range, the float pairs only float32's:
+  // each element's X is scaled by a power of two that brings its largest
+  // magnitude near 1 before the conversion, and Y is scaled back (both exact)
+  static constexpr bool kScaleIO = true;
   static constexpr int kTiles = 1;
   // Resident warps per SM the launcher aims at for the trilinear kinds at
   // N1 = 8 (by padding the dynamic shared memory): more warps thrash the
@@ -426,18 +431,51 @@ struct Geometry {
 };
 
 
+// Power-of-two scaling of an element's float64 values (policies with
+// kScaleIO).  emax is the largest biased exponent field among the element's
+// values; the shift d brings the largest magnitude into [1, 2) (clamped so
+// that 2^d and 2^-d are normal doubles).  Elements of zeros (emax 0) or with
+// an infinity or NaN (emax 0x7ff) are not scaled.
+__device__ __forceinline__ int io_shift(int emax) {
+  if (emax == 0 || emax == 0x7ff) return 0;
+  const int d = 1023 - emax;
+  return d < -1022 ? -1022 : (d > 1022 ? 1022 : d);
+}
+__device__ __forceinline__ double pow2i(int d) { return __hiloint2double((1023 + d) << 20, 0); }
+__device__ __forceinline__ int exp_field(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+__device__ __forceinline__ int exp_field(float v) { return (__float_as_int(v) >> 23) & 0xff; }
+// Direct range of the double-word kernels: zero (and float64 subnormals,
+// read as zero) or a magnitude in [2^-60, 2^61).  Within it the float pairs
+// and every intermediate of the product stay normal floats for element
+// extents in [2^-20, 2^24] (checked at setup).
+__device__ __forceinline__ bool in_direct_range(double v) {
+  const int ex = exp_field(v);
+  return ex == 0 || (unsigned)(ex - (1023 - 60)) <= 120u;
+}
+__device__ __forceinline__ bool in_direct_range(float) { return true; }
+
 // Coalesced copy of a block of values (contiguous in HBM) into padded
 // shared-memory rows of N1 values (pitch PITCH), converted by the policy P:
 // value m goes to row m / N1 at i = m % N1.  Consecutive threads read
 // consecutive 16-byte vectors when the values come in whole vectors and the
 // pointer is 16-byte aligned, else consecutive words.  THREADS * N1 >= nvals.
 template <class P, int N1, int PITCH, int THREADS>
-__device__ __forceinline__ void load_rows(const typename P::IO *__restrict__ src, int nvals, typename P::S *xs,
-                                          int tid) {
+__device__ __forceinline__ bool load_rows(const typename P::IO *__restrict__ src, int nvals, typename P::S *xs,
+                                          int tid, const int *emax) {
+  // emax (kScaleIO policies, or nullptr): per-element largest exponent field;
+  // each value is scaled by its element's power of two.  Without it the
+  // return value says whether a nonzero value lay outside the direct range.
   using IO = typename P::IO;
   constexpr int n3 = N1 * N1 * N1, VEC = 16 / (int)sizeof(IO);
+  bool wide = false;
   auto put = [&](int m, IO v) {
     const int row = m / N1;
+    if constexpr (P::kScaleIO) {
+      if (emax)
+        v = v * pow2i(io_shift(emax[m / n3]));
+      else
+        wide |= !in_direct_range(v);
+    }
     xs[row * PITCH + (m - row * N1)] = P::st(P::from_io(v));
   };
   if constexpr (n3 % VEC == 0) {
@@ -454,7 +492,7 @@ __device__ __forceinline__ void load_rows(const typename P::IO *__restrict__ src
           for (int c = 0; c < VEC; ++c) put(mv * VEC + c, pv[c]);
         }
       }
-      return;
+      return wide;
     }
   }
 #pragma unroll
@@ -462,6 +500,7 @@ __device__ __forceinline__ void load_rows(const typename P::IO *__restrict__ src
     const int m = tid + s * THREADS;
     if (m < nvals) put(m, src[m]);
   }
+  return wide;
 }
 
 template <int KIND>
@@ -500,6 +539,16 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   const typename P::C *cw = c_w + tab_off_v(N1);
   const typename P::C *cx = c_x + tab_off_v(N1);
   const int64_t nblk = (E + EPB - 1) / EPB;
+  // kScaleIO: largest exponent field of each element's X (slow path only,
+  // reset after use) and the shift its X entered with (X * 2^sshift[z]; 0
+  // unless the block took the scaled path)
+  __shared__ int sexp[P::kScaleIO ? EPB : 1];
+  __shared__ int sshift[P::kScaleIO ? EPB : 1];
+  static_assert(!P::kScaleIO || P::kRoll, "X/Y scaling is implemented in the rolled kernel body");
+  if constexpr (P::kScaleIO) {
+    if (tid < EPB) sexp[tid] = sshift[tid] = 0;
+    __syncthreads();
+  }
 
   // persistent over blocks of EPB elements (one block per CTA when gridDim covers nblk)
   for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
@@ -520,24 +569,62 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   // increase that halves the resident CTAs, 23% slower for float32 N = 15
   // (the compiler raises the register count at every N1 >= 11 of the float32
   // kernels with it).
+  constexpr bool kRowsCoalesced =
+      (sizeof(typename P::IO) == 4 && (N1 == 2 || N1 == 4 || N1 == 8)) || (P::kRoll && N1 == 16);
+  bool wide = false;  // kScaleIO: a nonzero value of this thread lies outside the direct range
   {
     using IO = typename P::IO;
     const IO *src = X + e0 * n3;
-    if constexpr ((sizeof(IO) == 4 && (N1 == 2 || N1 == 4 || N1 == 8)) || (P::kRoll && N1 == 16)) {
-      load_rows<P, N1, Sh::P, Sh::threads>(src, nel * n3, xs, tid);
+    if constexpr (kRowsCoalesced) {
+      wide = load_rows<P, N1, Sh::P, Sh::threads>(src, nel * n3, xs, tid, nullptr);
     } else {
       for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
         const IO *srow = src + (int64_t)row * N1;
         S *dst = xs + row * Sh::P;
 #pragma unroll
-        for (int i = 0; i < N1; ++i) dst[i] = P::st(P::from_io(srow[i]));
+        for (int i = 0; i < N1; ++i) {
+          const IO v = srow[i];
+          if constexpr (P::kScaleIO) wide |= !in_direct_range(v);
+          dst[i] = P::st(P::from_io(v));
+        }
       }
     }
   }
   if constexpr (GW > 0) {
     for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
   }
-  __syncthreads();
+  if constexpr (P::kScaleIO) {
+    // Blocks whose X stays inside the direct range (the normal case) go on
+    // at once.  Otherwise (CTA-uniform branch) each element's X is read
+    // again, scaled by the power of two that brings its largest magnitude
+    // into [1, 2), and Y is scaled back at the store.
+    const bool any_wide = __syncthreads_or(wide);
+    if (tid < EPB) sshift[tid] = 0;  // the previous block's Y stores all came before the barrier
+    if (any_wide) {
+      if (live) {
+        const typename P::IO *srow = X + e * n3 + q * N1;  // row q of element z
+        int mx = 0;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) mx = max(mx, exp_field(srow[i]));
+        atomicMax(&sexp[z], mx);
+      }
+      __syncthreads();
+      if constexpr (kRowsCoalesced) {
+        load_rows<P, N1, Sh::P, Sh::threads>(X + e0 * n3, nel * n3, xs, tid, sexp);
+      } else if (live) {
+        const typename P::IO *srow = X + e * n3 + q * N1;
+        S *dst = xs + tid * Sh::P;  // row tid = row q of element z
+        const typename P::IO sc = (typename P::IO)pow2i(io_shift(sexp[z]));
+#pragma unroll
+        for (int i = 0; i < N1; ++i) dst[i] = P::st(P::from_io(srow[i] * sc));
+      }
+      if (live && q == 0) sshift[z] = io_shift(sexp[z]);
+      __syncthreads();
+      if (tid < EPB) sexp[tid] = 0;  // every read of sexp came before the barrier
+    }
+  } else {
+    __syncthreads();
+  }
   if constexpr (AXS) {
     // threads q < 2 N1 of each element: the N1 r-axis and N1 s-axis terms,
     // read by every thread's geometry prologue after the next barriers
@@ -622,11 +709,14 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     __syncthreads();  // every Y_r, Y_s value is in B0, B1
     if (live) {
       typename P::IO *ye = Y + e * n3 + qa + N1 * qb;
+      // kScaleIO: undo the element's input shift (1.0 unless it took the scaled path)
+      const typename P::IO ysc = P::kScaleIO ? (typename P::IO)pow2i(-sshift[z]) : typename P::IO(1);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
         const V ytk = kYtRegs ? yt[kYtRegs ? k : 0] : P::ld(x_e + sidx);
-        ye[k * N1 * N1] = P::sum3_io(ytk, P::ld(r_e + sidx), P::ld(s_e + sidx));
+        const typename P::IO yv = P::sum3_io(ytk, P::ld(r_e + sidx), P::ld(s_e + sidx));
+        ye[k * N1 * N1] = P::kScaleIO ? yv * ysc : yv;
       }
     }
   } else {

@@ -91,8 +91,17 @@ __device__ void factors_from_J(const double J[9], double W, double g[7]) {
   g[6] = W * det;
 }
 
-// One thread per node.  flags[0] += nodes with det J <= 0.
-__global__ void validate_kernel(int64_t E, int N1, const double *__restrict__ V, int *flags) {
+// Element extents the FP32-based formats (float32, double-word pairs) handle
+// at full accuracy: the trilinear geometry forms products of up to four
+// Jacobian entries (adj(J^T J)); with entries of size L/2 these stay inside
+// float32's normal range, low words and error terms included, for element
+// extents L in [2^-20, 2^24] (adj ~ L^4 between about 2^-84 and 2^92).
+constexpr double kMinExtent = 0x1p-20, kMaxExtent = 0x1p24;
+
+// One thread per node.  flags[0] += nodes with det J <= 0; for the
+// FP32-based formats flags[3] += elements whose extent (largest vertex
+// coordinate difference from vertex 0) lies outside [kMinExtent, kMaxExtent].
+__global__ void validate_kernel(int64_t E, int N1, const double *__restrict__ V, int fmt, int *flags) {
   const int64_t n3 = (int64_t)N1 * N1 * N1;
   const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= E * n3) return;
@@ -102,6 +111,13 @@ __global__ void validate_kernel(int64_t E, int N1, const double *__restrict__ V,
   double J[9];
   map_jacobian(V + 24 * e, cx[i], cx[j], cx[k], J);
   if (!(det3(J) > 0.0)) atomicAdd(&flags[0], 1);
+  if (fmt != kF64 && l == 0) {
+    const double *Ve = V + 24 * e;
+    double ext = 0.0;
+    for (int v = 1; v < 8; ++v)
+      for (int c = 0; c < 3; ++c) ext = fmax(ext, fabs(Ve[3 * v + c] - Ve[c]));
+    if (!(ext >= kMinExtent && ext <= kMaxExtent)) atomicAdd(&flags[3], 1);
+  }
 }
 
 // STORED: discrete Jacobian of Sec. 3.2 -- the derivative along each reference
@@ -278,7 +294,7 @@ cudaError_t setup_geometry(const Ctx &c, const double *V, void *geo, void *lam, 
   const int B = 256;
   if (c.E == 0) return cudaSuccess;
   if ((nodes + B - 1) / B > 0x7fffffffLL) return cudaErrorInvalidValue;
-  validate_kernel<<<grid_for(nodes, B), B, 0, s>>>(c.E, c.N1, V, flags);
+  validate_kernel<<<grid_for(nodes, B), B, 0, s>>>(c.E, c.N1, V, fmt, flags);
   switch (c.kind) {
     case AX_GEOM_STORED:
       stored_factors_kernel<<<grid_for(nodes, B), B, 0, s>>>(c.E, c.N1, V, geo, fmt, flags);

@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(TcShape<N1>::threads)
     // row): coalesced at N1 = 2, 4, 8 (row and column by shifts), one row per
     // thread elsewhere (the same rule as the fiber kernels, measured there)
     if constexpr (N1 == 2 || N1 == 4 || N1 == 8) {
-      fiber::load_rows<P, N1, Sh::P, Sh::threads>(X + e0 * n3, nel * n3, xs, tid);
+      fiber::load_rows<P, N1, Sh::P, Sh::threads>(X + e0 * n3, nel * n3, xs, tid, nullptr);
     } else {
       for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
         const float *src = X + e0 * n3 + (int64_t)row * N1;

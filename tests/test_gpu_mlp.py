@@ -70,19 +70,23 @@ def _rss(A, B):
 
 
 def _scales(Pq, X, T):
-    """Per-entry error scales of the forward output and the six gradients,
-    propagated through the network in absolute values (a term's error scale
-    is the size of the terms it sums, plus what its inputs already carry)."""
+    """Per-entry error scales of the forward output and the six gradients.
+    Forward: each layer's pre-activation scale is the root-sum-square of its
+    terms (plus the bias and what the layer's input already carries), and
+    gelu magnifies it by at most GELU_LIP.  Backward: dY is at most
+    (|Y| + |T|) / (M O) in size, and each back-propagated quantity gets the
+    root-sum-square of its terms (times GELU_LIP through gelu'), so that an
+    entry's scale is the size its terms give it, not a worst-case sum."""
     W1, b1, W2, b2, W3, b3 = Pq
     M, O = T.shape
     Z1 = np.sqrt((X * X) @ (W1 * W1).T) + np.abs(b1)
     H1 = GELU_LIP * Z1
-    Z2 = np.sqrt((H1 * H1) @ (W2 * W2).T) + np.abs(b2) + H1 @ np.abs(W2).T * U_BF16
+    Z2 = np.sqrt((H1 * H1) @ (W2 * W2).T) + np.abs(b2)
     H2 = GELU_LIP * Z2
-    Y = np.sqrt((H2 * H2) @ (W3 * W3).T) + np.abs(b3) + H2 @ np.abs(W3).T * U_BF16
+    Y = np.sqrt((H2 * H2) @ (W3 * W3).T) + np.abs(b3)
     dY = (Y + np.abs(T)) / (M * O)
-    dZ2 = (dY @ np.abs(W3)) * (GELU_LIP + Z2)
-    dZ1 = (dZ2 @ np.abs(W2)) * (GELU_LIP + Z1)
+    dZ2 = np.sqrt((dY * dY) @ (W3 * W3)) * GELU_LIP
+    dZ1 = np.sqrt((dZ2 * dZ2) @ (W2 * W2)) * GELU_LIP
     return Y, [_rss(dZ1, X), np.sqrt((dZ1 * dZ1).sum(0)), _rss(dZ2, H1), np.sqrt((dZ2 * dZ2).sum(0)),
                _rss(dY, H2), np.sqrt((dY * dY).sum(0))]
 
