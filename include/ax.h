@@ -229,23 +229,51 @@ ax_status ax_batch_setup(ax_batch **out, int B, const int64_t *E, const int *N, 
 ax_status ax_batch_sizes(const ax_batch *b, int64_t *n_local, int64_t *n_global, int64_t *local_offsets,
                          int64_t *global_offsets);
 
-/* AxLocal of every mesh: X, Y device batch local vectors.  One launch per
- * distinct order. */
+/* AxLocal of every mesh: X, Y device batch local vectors.
+ * AX_FP32 batches of orders N <= 9 run as ONE persistent launch: a device
+ * queue of (mesh, element tile) items over all orders, dequeued by the CTAs
+ * (the paper runs one (E, N) per launch, Sec. 5.1; this goes beyond it).
+ * Other batches: one launch per distinct order (ax_batch_info tells which). */
 ax_status ax_batch_local(ax_batch *b, const void *X, void *Y, void *stream);
 
-/* Autotune, per group (order, geometry kind), the tile (elements per CTA:
- * 0 = base, 1 = twice, FP32 only) and the grid (0 = one CTA per element
- * block, else a persistent grid of k * SMs CTAs) by timing the group's
- * AxLocal; the choice is kept by the batch.  tiles, grids: host arrays with
- * one entry per group (or NULL).  Synchronises. */
+/* Autotune and keep the choice.  Persistent batches: element blocks per
+ * AxLocal item for each order group ({1, 2, 4, 8}, coordinate descent) and
+ * the grid (CTAs per SM: the occupancy limit or 1, 2, 4), timing the whole
+ * batch's single launch; tiles[g] gets the blocks per item, grids[g] the
+ * CTAs.  Other batches, per group: the tile (elements per CTA: 0 = base,
+ * 1 = twice, FP32 only) and the grid (0 = one CTA per element block, else a
+ * persistent grid of k * SMs CTAs).  tiles, grids: host arrays with one
+ * entry per group (or NULL).  Synchronises. */
 ax_status ax_batch_tune(ax_batch *b, int *tiles, int64_t *grids, void *stream);
+
+/* Choose the persistent single launch (on = 1, the default where it exists)
+ * or one launch per order group and per CG phase (on = 0).  AX_EUNSUPPORTED
+ * when the batch has no persistent kernel (not AX_FP32, or an order N > 9). */
+ax_status ax_batch_set_persistent(ax_batch *b, int on);
+
+/* Launches per ax_batch_local and per CG iteration of ax_batch_pcg
+ * (graph = 1) in the batch's current mode; *persistent = 1 in the
+ * persistent mode.  Any pointer may be NULL. */
+ax_status ax_batch_info(const ax_batch *b, int *persistent, int *local_launches, int *iteration_launches);
+
+/* Persistent batches: bound of every dependency wait inside the single CG
+ * launch, in ns (default 2e9), and a test hook: stuck_mesh >= 0 makes that
+ * mesh's gather items wait for one AxLocal item more than exist, so the wait
+ * runs out; ax_batch_pcg then stops and returns AX_ETIMEOUT, and the batch
+ * stays usable (-1 restores the normal dependency).  The paper has no
+ * counterpart.  AX_EUNSUPPORTED without a persistent kernel. */
+ax_status ax_batch_set_wait(ax_batch *b, int64_t budget_ns, int stuck_mesh);
 
 /* Independent Jacobi-PCG solves of every mesh's Dirichlet Poisson system.
  *   b_global, x_global: device batch global vectors (x: initial guess in,
  *   solutions out).  Per-mesh stop at ||r|| <= rtol ||b||.
  *   graph = 1: all meshes advance together; one CG iteration of the whole
  *   batch is captured once as a CUDA graph and launched once per iteration
- *   (per-mesh scalars, segmented reductions, converged meshes idle).
+ *   (per-mesh scalars, segmented reductions, converged meshes idle).  In
+ *   the persistent mode the graph holds ONE kernel: a queue of AxLocal
+ *   tiles (the scatter fused into their loads), gather + dot, update and
+ *   direction chunks, each waiting (bounded) for its mesh's previous phase;
+ *   a wait past its budget stops the solve with AX_ETIMEOUT.
  *   graph = 0: reference path, each mesh solved in turn with its own
  *   launches (pcg_solve on its per-mesh context).
  *   iters, relres: host arrays [B].  AX_ENOTCONV if a mesh hit maxit.

@@ -75,6 +75,12 @@ _lib.ax_batch_tune.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64), 
 _lib.ax_batch_tune.restype = _int
 _lib.ax_batch_pcg.argtypes = [_vp, _vp, _vp, _dbl, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_dbl), _vp]
 _lib.ax_batch_pcg.restype = _int
+_lib.ax_batch_set_persistent.argtypes = [_vp, _int]
+_lib.ax_batch_set_persistent.restype = _int
+_lib.ax_batch_info.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]
+_lib.ax_batch_info.restype = _int
+_lib.ax_batch_set_wait.argtypes = [_vp, _i64, _int]
+_lib.ax_batch_set_wait.restype = _int
 _lib.ax_batch_last_error.argtypes = [_vp]
 _lib.ax_batch_last_error.restype = ctypes.c_char_p
 _lib.ax_batch_destroy.argtypes = [_vp]
@@ -325,6 +331,18 @@ class AxBatch:
         if check and st not in (AX_OK, AX_ENOTCONV):
             _bcheck(st, self.b)
         return list(it), list(rr), st
+
+    def ax_batch_set_persistent(self, on: bool):
+        _bcheck(_lib.ax_batch_set_persistent(self.b, int(bool(on))), self.b)
+
+    def ax_batch_info(self) -> dict:
+        """{"persistent": 0/1, "local_launches": L, "iteration_launches": I}."""
+        p, l, i = _int(0), _int(0), _int(0)
+        _bcheck(_lib.ax_batch_info(self.b, ctypes.byref(p), ctypes.byref(l), ctypes.byref(i)), self.b)
+        return {"persistent": p.value, "local_launches": l.value, "iteration_launches": i.value}
+
+    def ax_batch_set_wait(self, budget_ns: int, stuck_mesh: int = -1):
+        _bcheck(_lib.ax_batch_set_wait(self.b, int(budget_ns), int(stuck_mesh)), self.b)
 
     def ax_batch_destroy(self):
         if self.b:

@@ -53,6 +53,8 @@ void release(ax_ctx *c) {
   cudaFree(c->c.lam);
   cudaFree(c->c.hx);
   cudaFree(c->c.hy);
+  cudaFree(c->c.wide);
+  c->c.wide = nullptr;
   c->c.free_ws();
   cudaFree(c->vtx);
   cudaFree(c->c.diag64);
@@ -71,6 +73,7 @@ ax::AxArgs make_args(ax_ctx *c, const void *X, void *Y, void *stream) {
   a.kind = c->c.kind;
   a.geo = c->c.geo;
   a.lam = c->c.lam;
+  a.wide = c->c.wide;
   a.X = X;
   a.Y = Y;
   a.stream = (cudaStream_t)stream;
@@ -163,6 +166,8 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
   const int64_t N1 = N + 1, n3 = N1 * N1 * N1;
   if (E > (int64_t)1 << 40 || E * n3 > ((int64_t)1 << 46))
     return fail(nullptr, AX_EINVAL, "ax_setup: problem too large");
+  if (prec == AX_F64DW && E > 2147483645LL)
+    return fail(nullptr, AX_ERANGE, "ax_setup: AX_F64DW takes at most 2^31 - 3 elements");
 
   ax_ctx *c = new (std::nothrow) ax_ctx;
   if (!c) return fail(nullptr, AX_ENOMEM, "ax_setup: host allocation failed");
@@ -212,6 +217,11 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
     e = cudaMalloc(&c->c.geo, c->c.geo_bytes);
     if (e == cudaSuccess && c->c.lam_bytes) e = cudaMalloc(&c->c.lam, c->c.lam_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->vtx, (size_t)E * 24 * sizeof(double));
+    if (e == cudaSuccess && prec == AX_F64DW) {
+      // block list of the double-word kernel's scaled fix-up pass, zero at rest
+      e = cudaMalloc(&c->c.wide, (size_t)(E + 2) * sizeof(int));
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->c.wide, 0, (size_t)(E + 2) * sizeof(int), s);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&flags, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->vtx, vertices, (size_t)E * 24 * sizeof(double), cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "ax_internal.h"
+#include "ax_persist.h"
 
 namespace ax {
 namespace batch {
@@ -246,6 +247,9 @@ struct ax_batch {
   int64_t *blo = nullptr, *bhi = nullptr;
   int *pbeg = nullptr;
   cudaStream_t cs = nullptr;  // private stream: graph capture needs a non-legacy stream
+  // one persistent launch for AxLocal and per CG iteration (float32, N <= 9)
+  persist::Plan *ps = nullptr;
+  bool use_persist = false;
   std::string err;
 };
 
@@ -269,6 +273,11 @@ ax_status bcuda(ax_batch *b, cudaError_t e, const char *what) {
 bool f64_prec(ax_precision p) { return p == AX_FP64 || p == AX_F64DW; }
 
 void batch_release(ax_batch *b) {
+  if (b->ps) {
+    persist::plan_free(*b->ps);
+    delete b->ps;
+    b->ps = nullptr;
+  }
   for (auto &g : b->groups) ax_destroy(g.ctx);
   for (auto *c : b->mesh_ctx) ax_destroy(c);
   b->groups.clear();
@@ -443,6 +452,44 @@ ax_status ax_batch_setup(ax_batch **out, int B, const int64_t *E, const int *N, 
     if (e == cudaSuccess) e = cudaMemcpy(b->pbeg, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
+  // the persistent plan: groups, meshes' element ranges, the segmentation
+  if (e == cudaSuccess && persist::supported(prec, b->N)) {
+    b->ps = new (std::nothrow) persist::Plan;
+    if (!b->ps) e = cudaErrorMemoryAllocation;
+  }
+  if (e == cudaSuccess && b->ps) {
+    persist::Plan &pl = *b->ps;
+    pl.kind = (int)kind;
+    pl.B = B;
+    pl.mesh_group.assign(B, 0);
+    pl.mesh_e0.assign(B, 0);
+    pl.mesh_E.assign(B, 0);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+      const auto &g = b->groups[gi];
+      const Ctx &core = ax_ctx_core(g.ctx);
+      persist::Group pg;
+      pg.N1 = g.N + 1;
+      pg.E = g.E;
+      pg.loc = g.loc_begin;
+      pg.geo = core.geo;
+      pg.lam = core.lam;
+      pl.groups.push_back(pg);
+      int64_t at = 0;
+      for (int m : g.meshes) {
+        pl.mesh_group[m] = (int)gi;
+        pl.mesh_e0[m] = at;
+        pl.mesh_E[m] = E[m];
+        at += E[m];
+      }
+    }
+    pl.sc.n_chunks = b->nblk;
+    pl.sc.cmesh = b->bmesh;
+    pl.sc.clo = b->blo;
+    pl.sc.chi = b->bhi;
+    pl.sc.pbeg = b->pbeg;
+    e = persist::plan_build(pl, s);
+    b->use_persist = e == cudaSuccess;
+  }
   if (e != cudaSuccess) {
     ax_status r = bcuda(nullptr, e, "ax_batch_setup");
     batch_release(b);
@@ -468,6 +515,11 @@ ax_status ax_batch_sizes(const ax_batch *b, int64_t *n_local, int64_t *n_global,
 ax_status ax_batch_local(ax_batch *b, const void *X, void *Y, void *stream) {
   if (!b) return bfail(nullptr, AX_EINVAL, "ax_batch_local: batch is NULL");
   if (!X || !Y) return bfail(b, AX_EINVAL, "ax_batch_local: NULL vector");
+  if (b->use_persist) {
+    cudaError_t e = persist::launch_local(*b->ps, (const float *)X, (float *)Y, (cudaStream_t)stream);
+    if (e != cudaSuccess) return bcuda(b, e, "ax_batch_local");
+    return AX_OK;
+  }
   cudaError_t (*L)(const AxArgs &) = launcher(b->prec);
   for (auto &g : b->groups) {
     cudaError_t e = L(group_args(b, g, X, Y, (cudaStream_t)stream));
@@ -476,9 +528,86 @@ ax_status ax_batch_local(ax_batch *b, const void *X, void *Y, void *stream) {
   return AX_OK;
 }
 
+namespace {
+
+// Persistent mode: element blocks per AxLocal item for each order group
+// (coordinate descent over {1, 2, 4, 8}, groups in turn) and the grid (CTAs
+// per SM: the occupancy limit or 1, 2, 4), by timing the whole batch's
+// single AxLocal launch.
+ax_status tune_persist(ax_batch *b, int *tiles, int64_t *grids, cudaStream_t s) {
+  persist::Plan &pl = *b->ps;
+  void *X = nullptr, *Y = nullptr;
+  cudaError_t e = cudaMalloc(&X, sizeof(float) * b->n_local);
+  if (e == cudaSuccess) e = cudaMalloc(&Y, sizeof(float) * b->n_local);
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, sizeof(float) * b->n_local, s);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  auto time_it = [&](float *ms) -> cudaError_t {
+    cudaError_t r = persist::plan_build(pl, s);
+    for (int q = 0; q < 2 && r == cudaSuccess; ++q) r = persist::launch_local(pl, (const float *)X, (float *)Y, s);
+    if (r == cudaSuccess) r = cudaEventRecord(t0, s);
+    for (int q = 0; q < 5 && r == cudaSuccess; ++q) r = persist::launch_local(pl, (const float *)X, (float *)Y, s);
+    if (r == cudaSuccess) r = cudaEventRecord(t1, s);
+    if (r == cudaSuccess) r = cudaEventSynchronize(t1);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(ms, t0, t1);
+    return r;
+  };
+  float best = 0.0f;
+  if (e == cudaSuccess) {
+    pl.tile_blocks.assign(pl.groups.size(), 1);
+    pl.grid_mult = 0;
+    e = time_it(&best);
+  }
+  const int tile_opts[] = {1, 2, 4, 8};
+  for (size_t g = 0; g < pl.groups.size() && e == cudaSuccess; ++g) {
+    const int keep = pl.tile_blocks[g];
+    int pick = keep;
+    for (int t : tile_opts) {
+      if (t == keep) continue;
+      pl.tile_blocks[g] = t;
+      float ms = 0.0f;
+      e = time_it(&ms);
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        pick = t;
+      }
+    }
+    pl.tile_blocks[g] = pick;
+  }
+  const int grid_opts[] = {1, 2, 4};
+  int gpick = 0;
+  for (int gm : grid_opts) {
+    if (e != cudaSuccess) break;
+    pl.grid_mult = gm;
+    float ms = 0.0f;
+    e = time_it(&ms);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      gpick = gm;
+    }
+  }
+  pl.grid_mult = gpick;
+  if (e == cudaSuccess) e = persist::plan_build(pl, s);
+  for (size_t g = 0; g < pl.groups.size(); ++g) {
+    if (tiles) tiles[g] = pl.tile_blocks[g];
+    if (grids) grids[g] = persist::plan_grid(pl);
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(X);
+  cudaFree(Y);
+  if (e != cudaSuccess) return bcuda(b, e, "ax_batch_tune");
+  return AX_OK;
+}
+
+}  // namespace
+
 ax_status ax_batch_tune(ax_batch *b, int *tiles, int64_t *grids, void *stream) {
   if (!b) return bfail(nullptr, AX_EINVAL, "ax_batch_tune: batch is NULL");
   cudaStream_t s = (cudaStream_t)stream;
+  if (b->use_persist) return tune_persist(b, tiles, grids, s);
   const size_t w = f64_prec(b->prec) ? 8 : 4;
   void *X = nullptr, *Y = nullptr;
   cudaError_t e = cudaMalloc(&X, w * b->n_local);
@@ -617,23 +746,45 @@ ax_status batch_pcg(ax_batch *b, const T *bvec, T *x, double rtol, int maxit, in
     seg_start<<<(B + 127) / 128, 128, 0, s>>>(B, W.S, rtol);
     e = cudaGetLastError();
   }
-  // capture one iteration
+  // capture one iteration: one persistent launch (float32, N <= 9) or the
+  // per-phase launches
+  const bool one_launch = sizeof(T) == 4 && b->use_persist;
+  persist::Vecs pv;
+  if (one_launch) {
+    pv.p = (float *)W.p;
+    pv.z = (float *)W.z;
+    pv.r = (float *)W.r;
+    pv.x = (float *)x;
+    pv.w = (float *)W.w;
+    pv.Yl = (float *)W.Yl;
+    pv.inv = (const float *)W.inv;
+    pv.gid = P.gid;
+    pv.off = P.off;
+    pv.idx = P.idx;
+    pv.mask = P.mask;
+    pv.S = W.S;
+    pv.part = W.part;
+    if (e == cudaSuccess) e = persist::plan_reset(*b->ps, s);
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e2 = batch_iteration<T>(b, W, x, s);
+    cudaError_t e2 = one_launch ? persist::launch_iteration(*b->ps, pv, s) : batch_iteration<T>(b, W, x, s);
     e = cudaStreamEndCapture(s, &graph);
     if (e == cudaSuccess) e = e2;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
   int issued = 0;
   bool all_done = false;
-  while (e == cudaSuccess && issued < maxit && !all_done) {
+  int pstatus = 0;  // persistent kernel: status word (AX_ETIMEOUT after a wait ran out)
+  while (e == cudaSuccess && issued < maxit && !all_done && pstatus == 0) {
     const int block = std::min(16, maxit - issued);
     for (int q = 0; q < block && e == cudaSuccess; ++q) e = cudaGraphLaunch(gexec, s);
     issued += block;
     if (e == cudaSuccess) e = cudaMemcpyAsync(W.hS, W.S, sizeof(double) * kS * B, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && one_launch)
+      e = cudaMemcpyAsync(&pstatus, b->ps->sc.status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     all_done = true;
     for (int m = 0; m < B && e == cudaSuccess; ++m)
@@ -651,6 +802,11 @@ ax_status batch_pcg(ax_batch *b, const T *bvec, T *x, double rtol, int maxit, in
     relres[m] = sm[3] > 0.0 ? std::sqrt(sm[2] / sm[3]) : 0.0;
     if (!done || sm[7] < 0.0) ++not_conv;
   }
+  if (pstatus != 0 && e == cudaSuccess) {
+    // clear the status and abort words so the batch's next calls run
+    e = persist::plan_reset(*b->ps, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
   if (e == cudaSuccess) e = cudaEventRecord(ev, s);
@@ -659,6 +815,9 @@ ax_status batch_pcg(ax_batch *b, const T *bvec, T *x, double rtol, int maxit, in
   cudaFree(W.r); cudaFree(W.z); cudaFree(W.p); cudaFree(W.w); cudaFree(W.inv); cudaFree(W.Ul); cudaFree(W.Yl);
   cudaFree(W.dl); cudaFree(W.S); cudaFree(W.part); cudaFreeHost(W.hS);
   if (e != cudaSuccess) return bcuda(b, e, "ax_batch_pcg");
+  if (pstatus != 0)
+    return bfail(b, AX_ETIMEOUT,
+                 "ax_batch_pcg: a dependency wait of the persistent iteration ran past its budget; the solve stopped");
   if (not_conv) return bfail(b, AX_ENOTCONV, "ax_batch_pcg: " + std::to_string(not_conv) + " meshes not converged");
   return AX_OK;
 }
@@ -691,6 +850,36 @@ ax_status ax_batch_pcg(ax_batch *b, const void *b_global, void *x_global, double
       return bfail(b, st, std::string("ax_batch_pcg (per mesh): ") + ax_last_error(b->mesh_ctx[m]));
   }
   if (not_conv) return bfail(b, AX_ENOTCONV, "ax_batch_pcg: " + std::to_string(not_conv) + " meshes not converged");
+  return AX_OK;
+}
+
+ax_status ax_batch_set_persistent(ax_batch *b, int on) {
+  if (!b) return bfail(nullptr, AX_EINVAL, "ax_batch_set_persistent: batch is NULL");
+  if (on && !b->ps)
+    return bfail(b, AX_EUNSUPPORTED,
+                 "ax_batch_set_persistent: the persistent kernel takes AX_FP32 batches of orders N <= 9");
+  b->use_persist = on != 0;
+  return AX_OK;
+}
+
+ax_status ax_batch_info(const ax_batch *b, int *persistent, int *local_launches, int *iteration_launches) {
+  if (!b) return AX_EINVAL;
+  const int groups = (int)b->groups.size();
+  if (persistent) *persistent = b->use_persist ? 1 : 0;
+  if (local_launches) *local_launches = b->use_persist ? 1 : groups;
+  // grouped iteration: scatter, one AxLocal per group, gather + dot, 3 segmented
+  // sums, update, convergence test, direction
+  if (iteration_launches) *iteration_launches = b->use_persist ? 1 : groups + 7;
+  return AX_OK;
+}
+
+ax_status ax_batch_set_wait(ax_batch *b, int64_t budget_ns, int stuck_mesh) {
+  if (!b) return bfail(nullptr, AX_EINVAL, "ax_batch_set_wait: batch is NULL");
+  if (!b->ps) return bfail(b, AX_EUNSUPPORTED, "ax_batch_set_wait: the batch has no persistent kernel");
+  if (budget_ns <= 0 || stuck_mesh < -1 || stuck_mesh >= b->B)
+    return bfail(b, AX_EINVAL, "ax_batch_set_wait: budget must be positive, stuck_mesh in [-1, B)");
+  b->ps->sc.budget_ns = budget_ns;
+  b->ps->sc.stuck_mesh = stuck_mesh;
   return AX_OK;
 }
 

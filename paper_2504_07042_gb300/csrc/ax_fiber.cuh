@@ -434,25 +434,29 @@ struct Geometry {
 // Power-of-two scaling of an element's float64 values (policies with
 // kScaleIO).  emax is the largest biased exponent field among the element's
 // values; the shift d brings the largest magnitude into [1, 2) (clamped so
-// that 2^d and 2^-d are normal doubles).  Elements of zeros (emax 0) or with
-// an infinity or NaN (emax 0x7ff) are not scaled.
+// that 2^d and 2^-d are normal doubles).  Elements with an infinity or NaN
+// (emax 0x7ff) are not scaled.
 __device__ __forceinline__ int io_shift(int emax) {
-  if (emax == 0 || emax == 0x7ff) return 0;
+  if (emax == 0x7ff) return 0;
+  if (emax == 0) return 1022;  // zeros and float64 subnormals: brought up by 2^1022
   const int d = 1023 - emax;
   return d < -1022 ? -1022 : (d > 1022 ? 1022 : d);
 }
 __device__ __forceinline__ double pow2i(int d) { return __hiloint2double((1023 + d) << 20, 0); }
 __device__ __forceinline__ int exp_field(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 __device__ __forceinline__ int exp_field(float v) { return (__float_as_int(v) >> 23) & 0xff; }
-// Direct range of the double-word kernels: zero (and float64 subnormals,
-// read as zero) or a magnitude in [2^-60, 2^61).  Within it the float pairs
-// and every intermediate of the product stay normal floats for element
-// extents in [2^-20, 2^24] (checked at setup).
-__device__ __forceinline__ bool in_direct_range(double v) {
-  const int ex = exp_field(v);
-  return ex == 0 || (unsigned)(ex - (1023 - 60)) <= 120u;
+// Direct range of the double-word kernels, tested per row of N1 values on
+// the largest magnitude of the row, read from the upper 32 bits of the
+// float64 values (sign cleared, integer order = magnitude order): a row is
+// direct when it is all zero or its largest magnitude lies in
+// [2^-60, 2^61).  Within it the float pairs and every intermediate of the
+// product stay normal floats for element extents in [2^-20, 2^24] (checked
+// at setup); values far below their row's largest contribute below the
+// accuracy.
+__device__ __forceinline__ int mag_hi(double v) { return __double2hiint(v) & 0x7fffffff; }
+__device__ __forceinline__ bool row_direct(int hmax) {
+  return hmax == 0 || (hmax >= ((1023 - 60) << 20) && hmax < ((1023 + 61) << 20));
 }
-__device__ __forceinline__ bool in_direct_range(float) { return true; }
 
 // Coalesced copy of a block of values (contiguous in HBM) into padded
 // shared-memory rows of N1 values (pitch PITCH), converted by the policy P:
@@ -471,10 +475,11 @@ __device__ __forceinline__ bool load_rows(const typename P::IO *__restrict__ src
   auto put = [&](int m, IO v) {
     const int row = m / N1;
     if constexpr (P::kScaleIO) {
-      if (emax)
-        v = v * pow2i(io_shift(emax[m / n3]));
-      else
-        wide |= !in_direct_range(v);
+      if (emax) v = v * pow2i(io_shift(emax[m / n3]));
+    }
+    if constexpr (P::kScaleIO) {
+      // each value alone is its own "row" here
+      if (!emax) wide |= !row_direct(mag_hi(v));
     }
     xs[row * PITCH + (m - row * N1)] = P::st(P::from_io(v));
   };
@@ -508,54 +513,91 @@ struct GeoWords {
   static constexpr int value = (KIND == AX_GEOM_STORED) ? 0 : (KIND == AX_GEOM_PARALLELEPIPED ? kParWords : kVertexWords);
 };
 
+// Sources of X: in place (element e's values at X[e n3 + m]), or the local
+// copies of a global vector, X[m] = u[gid[m]] (the scatter Q u of Eq. 1,
+// fused into the load).
+template <typename IO>
+struct XDirect {
+  static constexpr bool kDirect = true;
+  const IO *__restrict__ p;
+  __device__ __forceinline__ IO operator[](int64_t m) const { return p[m]; }
+};
+template <typename IO>
+struct XGather {
+  static constexpr bool kDirect = false;
+  const IO *__restrict__ u;
+  const gidx *__restrict__ gid;
+  __device__ __forceinline__ IO operator[](int64_t m) const { return u[gid[m]]; }
+};
+
+// Shared-memory buffers of one block of EPB elements.
+// FILL: the block shape (kFillWarps for the per-order kernels).
+template <class P, int N1, int KIND, int EM, bool FILL = kFillWarps<P, N1, KIND>>
+struct FiberSmem {
+  using Sh = Shape<N1, EM, FILL>;
+  using S = typename P::S;
+  static constexpr int GW = GeoWords<KIND>::value, GWD = GW > 0 ? GW : 1;
+  static constexpr bool AXS = kShareAxis<P, N1, KIND>;
+  static constexpr int AXD = AXS ? 2 * N1 * Geometry<P, N1, KIND>::kAxisWords : 1;
+  S *xs;        // [3][EPB][ES]: x, x0, x1; later t / Y_t, r / Y_r, s / Y_s
+  S *sgeo;      // [EPB][GWD]: the elements' geometry records
+  S *sax;       // [EPB][AXD]: per-element axis terms of the trilinear geometry (AXS)
+  int *sexp;    // [EPB] largest exponent field of each element's X (scaled fix-up pass)
+  __host__ __device__ static constexpr size_t a16(size_t b) { return (b + 15) / 16 * 16; }
+  // all four carved from one 16-byte aligned buffer of `bytes` bytes
+  static constexpr size_t bytes = a16(sizeof(S) * 3 * Sh::EPB * Sh::ES) + a16(sizeof(S) * Sh::EPB * GWD) +
+                                  a16(sizeof(S) * Sh::EPB * AXD) + a16(sizeof(int) * Sh::EPB);
+  __device__ static __forceinline__ FiberSmem carve(unsigned char *raw) {
+    FiberSmem m;
+    m.xs = (S *)raw;
+    raw += a16(sizeof(S) * 3 * Sh::EPB * Sh::ES);
+    m.sgeo = (S *)raw;
+    raw += a16(sizeof(S) * Sh::EPB * GWD);
+    m.sax = (S *)raw;
+    raw += a16(sizeof(S) * Sh::EPB * AXD);
+    m.sexp = (int *)raw;
+    return m;
+  }
+};
+
 // ---------------------------------------------------------------------------
-// the kernel.  Tables (per translation unit, constant memory):
-//   c_eoD / c_eoDT: even-odd blocks of D and D^T, c_w, c_x: weights, points.
+// AxLocal of one block of elements [e0, e0 + nel), nel <= EPB, by the CTA's
+// threads (Algorithm 1 with the geometry of Algorithms 2 and 3).  Tables
+// (per translation unit, constant memory): c_eoD / c_eoDT even-odd blocks of
+// D and D^T, c_w, c_x weights and points.  IDLE: the CTA may have more
+// threads than the order's shape (a CTA shaped for several orders); those
+// threads only take part in the barriers.
 // ---------------------------------------------------------------------------
-template <class P, int N1, int KIND, int EM>
-__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads, kMinCtas<P, N1, KIND>)
-    ax_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
-                    const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y) {
-  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
+template <class P, int N1, int KIND, int EM, bool IDLE, int SCALE, class XS, bool FILL = kFillWarps<P, N1, KIND>>
+__device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, FILL> &sm, const int tid, const int64_t e0,
+                                            const int nel, const typename P::S *__restrict__ geo,
+                                            const typename P::S *__restrict__ lam, const XS &X,
+                                            typename P::IO *__restrict__ Y) {
+  using Sh = Shape<N1, EM, FILL>;
+  using Buf = FiberSmem<P, N1, KIND, EM, FILL>;
   using V = typename P::V;
   using S = typename P::S;
   constexpr int n3 = Sh::n3, EPB = Sh::EPB, ES = Sh::ES;
   constexpr int GW = GeoWords<KIND>::value;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S *xs = (S *)smem_raw;       // [EPB][ES]: x, later Y
-  S *b0 = xs + EPB * ES;       // x0, later r
-  S *b1 = b0 + EPB * ES;       // x1, later s
-  __shared__ S sgeo[EPB][GW > 0 ? GW : 1];
-  // trilinear kinds: the per-element axis terms of the geometry (axis_terms)
-  constexpr bool AXS = kShareAxis<P, N1, KIND>;
+  static_assert(!IDLE || !P::kRoll, "idle threads are handled in the short (native) kernel body");
+  static_assert(SCALE == 0 || P::kScaleIO, "X scaling belongs to the policies with kScaleIO");
+  S *const xs = sm.xs;          // [EPB][ES]: x, later Y
+  S *const b0 = xs + EPB * ES;  // x0, later r
+  S *const b1 = b0 + EPB * ES;  // x1, later s
+  int *const sexp = sm.sexp;
+  constexpr bool AXS = Buf::AXS;
   constexpr int AXW = Geometry<P, N1, KIND>::kAxisWords;
-  __shared__ S sax[AXS ? EPB : 1][AXS ? 2 * N1 * AXW : 1];
-
-  const int tid = threadIdx.x;
+  const bool act = !IDLE || tid < Sh::threads;
   const int z = tid / Sh::F, q = tid % Sh::F;
   const int qa = q % N1, qb = q / N1;
   const typename P::C *eoD = c_eoD + tab_off_D(N1);
   const typename P::C *eoDT = c_eoDT + tab_off_D(N1);
   const typename P::C *cw = c_w + tab_off_v(N1);
   const typename P::C *cx = c_x + tab_off_v(N1);
-  const int64_t nblk = (E + EPB - 1) / EPB;
-  // kScaleIO: largest exponent field of each element's X (slow path only,
-  // reset after use) and the shift its X entered with (X * 2^sshift[z]; 0
-  // unless the block took the scaled path)
-  __shared__ int sexp[P::kScaleIO ? EPB : 1];
-  __shared__ int sshift[P::kScaleIO ? EPB : 1];
-  static_assert(!P::kScaleIO || P::kRoll, "X/Y scaling is implemented in the rolled kernel body");
-  if constexpr (P::kScaleIO) {
-    if (tid < EPB) sexp[tid] = sshift[tid] = 0;
-    __syncthreads();
-  }
-
-  // persistent over blocks of EPB elements (one block per CTA when gridDim covers nblk)
-  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-  const int64_t e0 = blk * EPB;
-  const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+  const S *const sgeo_z = sm.sgeo + (act ? z : 0) * Buf::GWD;
+  S *const sax_z = sm.sax + (act && AXS ? z : 0) * Buf::AXD;
   const int64_t e = e0 + z;
-  const bool live = z < nel;
+  const bool live = act && z < nel;
 
   // pass 0: the CTA's elements (contiguous in HBM) into padded shared memory.
   // Value m of the block sits in row m / N1 (row = j + N1 (k + N1 z) is also
@@ -569,66 +611,65 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   // increase that halves the resident CTAs, 23% slower for float32 N = 15
   // (the compiler raises the register count at every N1 >= 11 of the float32
   // kernels with it).
+  // (a gathered X, X[m] = u[gid[m]], is read one row per thread)
   constexpr bool kRowsCoalesced =
-      (sizeof(typename P::IO) == 4 && (N1 == 2 || N1 == 4 || N1 == 8)) || (P::kRoll && N1 == 16);
-  bool wide = false;  // kScaleIO: a nonzero value of this thread lies outside the direct range
-  {
+      XS::kDirect && ((sizeof(typename P::IO) == 4 && (N1 == 2 || N1 == 4 || N1 == 8)) || (P::kRoll && N1 == 16));
+  // Policies with kScaleIO (float64 data in float32 pairs) run in two modes.
+  // SCALE = 1, the main kernel: X is converted directly and the block
+  // reports whether a row's largest magnitude lies outside the direct range
+  // (row_direct).  SCALE = 2, a fix-up kernel over only the reported blocks:
+  // each element's X is scaled by the power of two that brings its largest
+  // magnitude into [1, 2) before the conversion, and its Y is scaled back.
+  bool wide = false;  // SCALE 1: a row of this thread lies outside the direct range
+  int xshift = 0;     // SCALE 2: this thread's element entered as X * 2^xshift
+  if constexpr (SCALE == 2) {
+    if (live) {
+      const int64_t srow = e * n3 + q * N1;  // row q of element z
+      int mx = 0;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) mx = max(mx, exp_field(X[srow + i]));
+      atomicMax(&sexp[z], mx);
+    }
+    __syncthreads();
+    if (live) xshift = io_shift(sexp[z]);
+  }
+  if (act) {
     using IO = typename P::IO;
-    const IO *src = X + e0 * n3;
     if constexpr (kRowsCoalesced) {
-      wide = load_rows<P, N1, Sh::P, Sh::threads>(src, nel * n3, xs, tid, nullptr);
+      wide = load_rows<P, N1, Sh::P, Sh::threads>(X.p + e0 * n3, nel * n3, xs, tid, SCALE == 2 ? sexp : nullptr);
     } else {
       for (int row = tid; row < nel * N1 * N1; row += Sh::threads) {
-        const IO *srow = src + (int64_t)row * N1;
+        const int64_t src = e0 * n3 + (int64_t)row * N1;
         S *dst = xs + row * Sh::P;
+        // SCALE 2: one row per thread (threads = EPB N1^2), row tid of element z
+        const IO sc = SCALE == 2 ? (IO)pow2i(xshift) : IO(1);
+        int hmax = 0;  // SCALE 1: the row's largest magnitude (upper 32 bits)
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
-          const IO v = srow[i];
-          if constexpr (P::kScaleIO) wide |= !in_direct_range(v);
-          dst[i] = P::st(P::from_io(v));
+          const IO v = X[src + i];
+          if constexpr (SCALE == 1) hmax = max(hmax, mag_hi(v));
+          dst[i] = P::st(P::from_io(SCALE == 2 ? v * sc : v));
         }
+        if constexpr (SCALE == 1) wide |= !row_direct(hmax);
       }
     }
-  }
-  if constexpr (GW > 0) {
-    for (int m = tid; m < nel * GW; m += Sh::threads) sgeo[m / GW][m % GW] = geo[e0 * GW + m];
-  }
-  if constexpr (P::kScaleIO) {
-    // Blocks whose X stays inside the direct range (the normal case) go on
-    // at once.  Otherwise (CTA-uniform branch) each element's X is read
-    // again, scaled by the power of two that brings its largest magnitude
-    // into [1, 2), and Y is scaled back at the store.
-    const bool any_wide = __syncthreads_or(wide);
-    if (tid < EPB) sshift[tid] = 0;  // the previous block's Y stores all came before the barrier
-    if (any_wide) {
-      if (live) {
-        const typename P::IO *srow = X + e * n3 + q * N1;  // row q of element z
-        int mx = 0;
-#pragma unroll
-        for (int i = 0; i < N1; ++i) mx = max(mx, exp_field(srow[i]));
-        atomicMax(&sexp[z], mx);
-      }
-      __syncthreads();
-      if constexpr (kRowsCoalesced) {
-        load_rows<P, N1, Sh::P, Sh::threads>(X + e0 * n3, nel * n3, xs, tid, sexp);
-      } else if (live) {
-        const typename P::IO *srow = X + e * n3 + q * N1;
-        S *dst = xs + tid * Sh::P;  // row tid = row q of element z
-        const typename P::IO sc = (typename P::IO)pow2i(io_shift(sexp[z]));
-#pragma unroll
-        for (int i = 0; i < N1; ++i) dst[i] = P::st(P::from_io(srow[i] * sc));
-      }
-      if (live && q == 0) sshift[z] = io_shift(sexp[z]);
-      __syncthreads();
-      if (tid < EPB) sexp[tid] = 0;  // every read of sexp came before the barrier
+    if constexpr (GW > 0) {
+      for (int m = tid; m < nel * GW; m += Sh::threads) sm.sgeo[(m / GW) * Buf::GWD + m % GW] = geo[e0 * GW + m];
     }
+  }
+  bool any_wide = false;
+  if constexpr (SCALE == 1) {
+    any_wide = __syncthreads_or(wide);
   } else {
     __syncthreads();
+  }
+  if constexpr (SCALE == 2) {
+    if (tid < EPB) sexp[tid] = 0;  // every read of sexp came before the barrier
   }
   if constexpr (AXS) {
     // threads q < 2 N1 of each element: the N1 r-axis and N1 s-axis terms,
     // read by every thread's geometry prologue after the next barriers
-    if (live && q < 2 * N1) Geometry<P, N1, KIND>::axis_terms(sgeo[z], cx, q / N1, q % N1, &sax[z][q * AXW]);
+    if (live && q < 2 * N1) Geometry<P, N1, KIND>::axis_terms(sgeo_z, cx, q / N1, q % N1, sax_z + q * AXW);
   }
 
   S *x_e = xs + z * ES, *r_e = b0 + z * ES, *s_e = b1 + z * ES;
@@ -663,8 +704,8 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     // thread (i, j) = (qa, qb): geometry and G x along its own t-fiber
     const int i = qa, j = qb;
     Geometry<P, N1, KIND> gm;
-    gm.template prologue<AXS>(sgeo[z], cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
-                              (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr, sax[AXS ? z : 0]);
+    gm.template prologue<AXS>(sgeo_z, cx, cw, i, j, (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
+                              (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr, sax_z);
     auto node = [&](int k) {
       const int sidx = ft + k * str_t;
       const V xv[3] = {P::ld(r_e + sidx), P::ld(s_e + sidx), P::ld(x_e + sidx)};
@@ -709,14 +750,19 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     __syncthreads();  // every Y_r, Y_s value is in B0, B1
     if (live) {
       typename P::IO *ye = Y + e * n3 + qa + N1 * qb;
-      // kScaleIO: undo the element's input shift (1.0 unless it took the scaled path)
-      const typename P::IO ysc = P::kScaleIO ? (typename P::IO)pow2i(-sshift[z]) : typename P::IO(1);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
         const V ytk = kYtRegs ? yt[kYtRegs ? k : 0] : P::ld(x_e + sidx);
-        const typename P::IO yv = P::sum3_io(ytk, P::ld(r_e + sidx), P::ld(s_e + sidx));
-        ye[k * N1 * N1] = P::kScaleIO ? yv * ysc : yv;
+        ye[k * N1 * N1] = P::sum3_io(ytk, P::ld(r_e + sidx), P::ld(s_e + sidx));
+      }
+      if constexpr (SCALE == 2) {
+        // undo the element's input shift on the values just stored (exact)
+        if (xshift != 0) {
+          const typename P::IO ysc = (typename P::IO)pow2i(-xshift);
+#pragma unroll 1
+          for (int k = 0; k < N1; ++k) ye[k * N1 * N1] *= ysc;
+        }
       }
     }
   } else {
@@ -726,11 +772,11 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     // products overwrite B0 and B1 in place (no read-modify-write of Y, no
     // barrier between them); the t-fiber owner sums Y = Y_t + Y_r + Y_s at
     // its nodes and stores it to HBM (for each k the warp writes consecutive
-    // i, j: coalesced).
-    forward(0);
-    forward(1);
+    // i, j: coalesced).  (IDLE threads skip every step but the barriers.)
     V tf[N1];
-    {
+    if (act) {
+      forward(0);
+      forward(1);
       V fin_[N1];
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(x_e + ft + n * str_t);
@@ -738,12 +784,12 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     }
     __syncthreads();  // every r/s fiber product is in B0, B1
     V yt[N1];
-    {
+    if (act) {
       const int i = qa, j = qb;
       Geometry<P, N1, KIND> gm;
-      gm.template prologue<AXS>(sgeo[z], cx, cw, i, j,
+      gm.template prologue<AXS>(sgeo_z, cx, cw, i, j,
                                 (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * n3 : nullptr,
-                                (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr, sax[AXS ? z : 0]);
+                                (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * n3 : nullptr, sax_z);
 #pragma unroll
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
@@ -763,6 +809,7 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
     __syncthreads();  // every r, s value is in B0, B1
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
+      if (!act) break;
       S *buf = d == 0 ? r_e : s_e;
       const int base = d == 0 ? fr : fs, stride = d == 0 ? str_r : str_s;
       V fin_[N1], fout[N1];
@@ -784,6 +831,78 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
   }
 
   __syncthreads();  // the next block reuses the shared buffers
+  return any_wide;
+}
+
+// ---------------------------------------------------------------------------
+// the per-order kernel: blocks of EPB elements, persistent over blocks when
+// the grid is capped (autotuner)
+// ---------------------------------------------------------------------------
+// wide: kScaleIO policies: list of the blocks whose X left the direct range
+// ([0] count, [1] exit counter of the fix-up kernel, [2..] block indices).
+template <class P, int N1, int KIND, int EM>
+__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads, kMinCtas<P, N1, KIND>)
+    ax_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
+                    const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y, int *__restrict__ wide) {
+  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
+  using Buf = FiberSmem<P, N1, KIND, EM>;
+  using S = typename P::S;
+  constexpr int EPB = Sh::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ S sgeo[EPB][Buf::GWD];
+  __shared__ S sax[Buf::AXS ? EPB : 1][Buf::AXD];
+  Buf sm;
+  sm.xs = (S *)smem_raw;
+  sm.sgeo = &sgeo[0][0];
+  sm.sax = &sax[0][0];
+  sm.sexp = nullptr;
+  const int tid = threadIdx.x;
+  const int64_t nblk = (E + EPB - 1) / EPB;
+  for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int64_t e0 = blk * EPB;
+    const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+    const bool w = fiber_block<P, N1, KIND, EM, false, P::kScaleIO ? 1 : 0>(sm, tid, e0, nel, geo, lam,
+                                                                           XDirect<typename P::IO>{X}, Y);
+    if constexpr (P::kScaleIO) {
+      if (w && tid == 0) wide[2 + atomicAdd(&wide[0], 1)] = (int)blk;
+    }
+  }
+}
+
+// The fix-up kernel of the kScaleIO policies: the listed blocks again, with X
+// scaled per element; the last CTA to finish clears the list.
+template <class P, int N1, int KIND, int EM>
+__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads)
+    ax_fiber_fix_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
+                        const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y, int *__restrict__ wide) {
+  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
+  using Buf = FiberSmem<P, N1, KIND, EM>;
+  using S = typename P::S;
+  constexpr int EPB = Sh::EPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ S sgeo[EPB][Buf::GWD];
+  __shared__ S sax[Buf::AXS ? EPB : 1][Buf::AXD];
+  __shared__ int sexp[EPB];
+  Buf sm;
+  sm.xs = (S *)smem_raw;
+  sm.sgeo = &sgeo[0][0];
+  sm.sax = &sax[0][0];
+  sm.sexp = sexp;
+  const int tid = threadIdx.x;
+  if (tid < EPB) sexp[tid] = 0;
+  __syncthreads();
+  const int cnt = *(volatile int *)&wide[0];
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int64_t e0 = (int64_t)wide[2 + i] * EPB;
+    const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+    fiber_block<P, N1, KIND, EM, false, 2>(sm, tid, e0, nel, geo, lam, XDirect<typename P::IO>{X}, Y);
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&wide[1], 1) == (int)gridDim.x - 1) {
+      wide[0] = 0;
+      wide[1] = 0;
+    }
   }
 }
 
@@ -822,6 +941,9 @@ __global__ void __launch_bounds__(Shape<N1, 1, kFillWarps<P, N1, KIND>>::threads
     G[(e * 7 + 6) * n3 + l] = (double)P::to_io(gwj);
   }
 }
+
+// CTAs of the fix-up kernel (a persistent loop over the listed blocks)
+constexpr int64_t kFixGrid = 256;
 
 template <class P, int N1, int KIND, int EM>
 cudaError_t launch_ax_em(const AxArgs &a) {
@@ -863,9 +985,25 @@ cudaError_t launch_ax_em(const AxArgs &a) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  if (P::kScaleIO && !a.wide) return cudaErrorInvalidValue;  // the context's block list is required
   ax_fiber_kernel<P, N1, KIND, EM><<<(unsigned)grid, Sh::threads, smem, a.stream>>>(
       a.E, (const typename P::S *)a.geo, (const typename P::S *)a.lam, (const typename P::IO *)a.X,
-      (typename P::IO *)a.Y);
+      (typename P::IO *)a.Y, a.wide);
+  if constexpr (P::kScaleIO) {
+    // the blocks whose X left the direct range, again with scaling (usually none)
+    static bool fix_attr = false;
+    const size_t fsmem = (size_t)3 * Sh::EPB * Sh::ES * sizeof(typename P::S);
+    if (!fix_attr) {
+      cudaError_t e = cudaFuncSetAttribute(ax_fiber_fix_kernel<P, N1, KIND, EM>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+      if (e != cudaSuccess) return e;
+      fix_attr = true;
+    }
+    const int64_t fgrid = nblk < kFixGrid ? nblk : kFixGrid;
+    ax_fiber_fix_kernel<P, N1, KIND, EM><<<(unsigned)fgrid, Sh::threads, fsmem, a.stream>>>(
+        a.E, (const typename P::S *)a.geo, (const typename P::S *)a.lam, (const typename P::IO *)a.X,
+        (typename P::IO *)a.Y, a.wide);
+  }
   return cudaGetLastError();
 }
 

@@ -50,6 +50,7 @@ struct Ctx {
   size_t geo_bytes = 0;
   void *lam = nullptr;
   size_t lam_bytes = 0;
+  int *wide = nullptr;  // AX_F64DW: block list of the scaled fix-up pass (int[2 + E], zeroed)
   // device staging buffers for ax_local_host
   void *hx = nullptr, *hy = nullptr;
   size_t hbytes = 0;
@@ -85,6 +86,9 @@ struct AxArgs {
   cudaStream_t stream = nullptr;
   int tile = 0;      // tile variant (elements per CTA: 0 = base, 1 = twice; FP32 only)
   int64_t grid = 0;  // CTAs to launch (0 = one per block of elements; fewer = persistent loop)
+  // double-word precision: the context's list of element blocks whose X left
+  // the kernel's direct range (int[2 + E], zero at rest; see ax_fiber.cuh)
+  int *wide = nullptr;
 };
 
 // Launchers (return cudaSuccess or the launch error).
