@@ -421,7 +421,9 @@ def run(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64dw", "data": "synthetic",
             "config": headline_config(world),
-            "roofline": roof_line, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
+            "roofline": roof_line, "e2e": e2e,
+            # per step: the AxLocal kernel and its scaled fix-up pass (an empty list: no work)
+            "gpu_launches": 2 * args.steps, "clocks": clocks}
     if rank == 0:
         rate, cores, sample = cpu_oracle_rate()
         rate1, sample1 = cpu_oracle_rate_single_thread()
@@ -521,10 +523,13 @@ def run_pcg(ax, torch, dev):
 
 def run_batch(ax, torch, dev):
     """64 perturbed-box meshes, E log-uniform on [64, 4096] (near-cubic boxes),
-    N uniform on {3,5,7,9}, FP32, trilinear recompute: batched AxLocal (one
-    launch per order) and batched Jacobi-PCG (one CUDA-graph launch per CG
-    iteration) against the per-mesh paths (one launch per mesh per step);
-    then the batched paths with TF32 tensor-core contractions."""
+    N uniform on {3,5,7,9}, FP32, trilinear recompute.  AxLocal of the whole
+    batch as ONE persistent launch over a (mesh, element tile) queue
+    (untuned and autotuned), against one launch per order group and one
+    launch per mesh; Jacobi-PCG to 1e-5 with one CUDA-graph launch per CG
+    iteration holding one persistent kernel, against the grouped graph (one
+    launch per phase and order) and the meshes solved in turn; then the
+    grouped path with TF32 tensor-core contractions."""
     from paper_2504_07042_gb300 import inputs
     spec = inputs.batch_meshes()
     meshes = []
@@ -549,18 +554,37 @@ def run_batch(ax, torch, dev):
         for op, xs, ys in slices:
             op.ax_local(xs, ys, stream)
 
-    untuned = _time_launches(torch, lambda: bt.ax_batch_local(X, Y, stream), 10, 3, stream)
+    local = lambda: bt.ax_batch_local(X, Y, stream)  # noqa: E731
+    info = bt.ax_batch_info()
+    untuned = _time_launches(torch, local, 10, 3, stream)
     tune = bt.ax_batch_tune()
-    batched = _time_launches(torch, lambda: bt.ax_batch_local(X, Y, stream), 10, 3, stream)
+    tuned = _time_launches(torch, local, 10, 3, stream)
+    bt.ax_batch_set_persistent(False)
+    grouped_untuned = _time_launches(torch, local, 10, 3, stream)
+    gtune = bt.ax_batch_tune()
+    grouped = _time_launches(torch, local, 10, 3, stream)
+    ginfo = bt.ax_batch_info()
+    bt.ax_batch_set_persistent(True)
     single = _time_launches(torch, per_mesh, 10, 3, stream)
+    gd = lambda ms: bt.n_local / (ms * 1e-3) / 1e9  # noqa: E731
     out = {"meshes": len(spec), "elements": int(sum(m[0].shape[0] for m in meshes)), "local_dofs": bt.n_local,
            "global_dofs": bt.n_global, "orders": sorted(set(int(m[1]) for m in meshes)),
-           "tuned_tile_grid_per_order": {str(k): list(v) for k, v in tune.items()},
-           "axlocal_batched_ms": batched, "axlocal_batched_untuned_ms": untuned, "axlocal_per_mesh_ms": single,
-           "axlocal_batched_gdofs": bt.n_local / (batched * 1e-3) / 1e9,
-           "axlocal_per_mesh_gdofs": bt.n_local / (single * 1e-3) / 1e9}
+           "persistent": {"launches_per_axlocal": info["local_launches"],
+                          "launches_per_cg_iteration": info["iteration_launches"],
+                          "tuned_blocks_per_item_and_grid_per_order": {str(k): list(v) for k, v in tune.items()},
+                          "axlocal_untuned_ms": untuned, "axlocal_tuned_ms": tuned,
+                          "autotune_saves_pct": 100.0 * (untuned - tuned) / untuned,
+                          "axlocal_tuned_gdofs": gd(tuned)},
+           "grouped": {"launches_per_axlocal": ginfo["local_launches"],
+                       "launches_per_cg_iteration": ginfo["iteration_launches"],
+                       "tuned_tile_grid_per_order": {str(k): list(v) for k, v in gtune.items()},
+                       "axlocal_untuned_ms": grouped_untuned, "axlocal_tuned_ms": grouped,
+                       "axlocal_tuned_gdofs": gd(grouped)},
+           "per_mesh": {"launches_per_axlocal": len(spec), "axlocal_ms": single, "axlocal_gdofs": gd(single)},
+           "speedup_persistent_over_per_mesh": single / tuned, "speedup_persistent_over_grouped": grouped / tuned}
     bvec = torch.ones(bt.n_global, device=dev, dtype=torch.float32)
-    for graph, name in ((1, "pcg_graph"), (0, "pcg_per_mesh")):
+
+    def solve(graph, name):
         x = torch.zeros_like(bvec)
         bt.ax_batch_pcg(bvec, x, rtol=1e-5, maxit=20000, graph=graph)  # warm-up
         x.zero_()
@@ -570,11 +594,19 @@ def run_batch(ax, torch, dev):
         torch.cuda.synchronize()
         out[name] = {"seconds": time.perf_counter() - t, "status": st, "max_iterations": max(it),
                      "total_iterations": sum(it), "max_relres": max(rr)}
-    out["pcg_speedup_graph_over_per_mesh"] = out["pcg_per_mesh"]["seconds"] / out["pcg_graph"]["seconds"]
+
+    solve(1, "pcg_graph_persistent")
+    bt.ax_batch_set_persistent(False)
+    solve(1, "pcg_graph_grouped")
+    bt.ax_batch_set_persistent(True)
+    solve(0, "pcg_per_mesh")
+    out["pcg_speedup_persistent_over_per_mesh"] = out["pcg_per_mesh"]["seconds"] / out["pcg_graph_persistent"]["seconds"]
+    out["pcg_speedup_persistent_over_grouped"] = (out["pcg_graph_grouped"]["seconds"]
+                                                  / out["pcg_graph_persistent"]["seconds"])
     for op in per:
         op.ax_destroy()
     bt.ax_batch_destroy()
-    # the same batch with TF32 tensor-core contractions (FP32 accumulation)
+    # the same batch with TF32 tensor-core contractions (FP32 accumulation): grouped launches
     bt = ax.AxBatch(meshes, "trilinear", "tf32")
     bt.ax_batch_tune()
     t_tc = _time_launches(torch, lambda: bt.ax_batch_local(X, Y, stream), 10, 3, stream)
@@ -585,9 +617,9 @@ def run_batch(ax, torch, dev):
     t = time.perf_counter()
     it, rr, st = bt.ax_batch_pcg(bvec, x, rtol=1e-5, maxit=20000, graph=1)
     torch.cuda.synchronize()
-    out["tf32"] = {"axlocal_batched_ms": t_tc, "axlocal_batched_gdofs": bt.n_local / (t_tc * 1e-3) / 1e9,
-                   "pcg_graph": {"seconds": time.perf_counter() - t, "status": st, "max_iterations": max(it),
-                                 "total_iterations": sum(it), "max_relres": max(rr)}}
+    out["tf32_grouped"] = {"axlocal_batched_ms": t_tc, "axlocal_batched_gdofs": gd(t_tc),
+                           "pcg_graph": {"seconds": time.perf_counter() - t, "status": st, "max_iterations": max(it),
+                                         "total_iterations": sum(it), "max_relres": max(rr)}}
     bt.ax_batch_destroy()
     return out
 

@@ -379,6 +379,13 @@ const char *ax_last_error(const ax_ctx *c);
 /* Name of a status code. */
 const char *ax_status_string(ax_status s);
 
+/* Status of the context's asynchronous work: synchronises `stream`, then
+ * returns AX_ETIMEOUT if a bounded wait inside one of the context's kernels
+ * ran out since the last check (the tensor-core AxLocal of AX_TF32 at N = 7
+ * waits on its MMAs, at most about 2 s; the output of that launch is void),
+ * else AX_OK.  Clears the record. */
+ax_status ax_check(ax_ctx *c, void *stream);
+
 /* Release everything the context owns.  NULL is accepted. */
 void ax_destroy(ax_ctx *c);
 

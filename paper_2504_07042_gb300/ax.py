@@ -75,6 +75,8 @@ _lib.ax_batch_tune.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64), 
 _lib.ax_batch_tune.restype = _int
 _lib.ax_batch_pcg.argtypes = [_vp, _vp, _vp, _dbl, _int, _int, ctypes.POINTER(_int), ctypes.POINTER(_dbl), _vp]
 _lib.ax_batch_pcg.restype = _int
+_lib.ax_check.argtypes = [_vp, _vp]
+_lib.ax_check.restype = _int
 _lib.ax_batch_set_persistent.argtypes = [_vp, _int]
 _lib.ax_batch_set_persistent.restype = _int
 _lib.ax_batch_info.argtypes = [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_int)]
@@ -258,6 +260,10 @@ class Ax:
         if check and st not in (AX_OK, AX_ENOTCONV):
             _check(st, self.ctx)
         return o.value, i.value, rr.value, st
+
+    def ax_check(self, stream=None):
+        """Synchronise and report a bounded wait that ran out (AxError AX_ETIMEOUT)."""
+        _check(_lib.ax_check(self.ctx, _stream(stream)), self.ctx)
 
     def ax_query(self) -> dict:
         info = ax_info()

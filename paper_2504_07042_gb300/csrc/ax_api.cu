@@ -55,6 +55,8 @@ void release(ax_ctx *c) {
   cudaFree(c->c.hy);
   cudaFree(c->c.wide);
   c->c.wide = nullptr;
+  cudaFree(c->c.kerr);
+  c->c.kerr = nullptr;
   c->c.free_ws();
   cudaFree(c->vtx);
   cudaFree(c->c.diag64);
@@ -74,6 +76,7 @@ ax::AxArgs make_args(ax_ctx *c, const void *X, void *Y, void *stream) {
   a.geo = c->c.geo;
   a.lam = c->c.lam;
   a.wide = c->c.wide;
+  a.err = c->c.kerr;
   a.X = X;
   a.Y = Y;
   a.stream = (cudaStream_t)stream;
@@ -217,6 +220,11 @@ ax_status ax_setup(ax_ctx **out, int64_t E, int N, const double *vertices, ax_ge
     e = cudaMalloc(&c->c.geo, c->c.geo_bytes);
     if (e == cudaSuccess && c->c.lam_bytes) e = cudaMalloc(&c->c.lam, c->c.lam_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->vtx, (size_t)E * 24 * sizeof(double));
+    if (e == cudaSuccess && prec == AX_TF32) {
+      // error word of the tensor-core kernel's bounded waits
+      e = cudaMalloc(&c->c.kerr, sizeof(int));
+      if (e == cudaSuccess) e = cudaMemsetAsync(c->c.kerr, 0, sizeof(int), s);
+    }
     if (e == cudaSuccess && prec == AX_F64DW) {
       // block list of the double-word kernel's scaled fix-up pass, zero at rest
       e = cudaMalloc(&c->c.wide, (size_t)(E + 2) * sizeof(int));
@@ -588,6 +596,21 @@ ax_status pcg_solve_mixed(ax_ctx *hi, ax_ctx *lo, const double *b_global, double
              *outer_iters, *inner_iters, *relres);
     return fail(hi, AX_ENOTCONV, msg);
   }
+  return AX_OK;
+}
+
+ax_status ax_check(ax_ctx *c, void *stream) {
+  if (!c) return fail(nullptr, AX_EINVAL, "ax_check: context is NULL");
+  if (!same_device(c)) return fail(c, AX_EINVAL, "ax_check: current device differs from the context's");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  int h = 0;
+  if (e == cudaSuccess && c->c.kerr) {
+    e = cudaMemcpy(&h, c->c.kerr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h) e = cudaMemset(c->c.kerr, 0, sizeof(int));
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "ax_check");
+  if (h) return fail(c, AX_ETIMEOUT, "ax_check: a bounded wait of the tensor-core AxLocal ran out; its output is void");
   return AX_OK;
 }
 

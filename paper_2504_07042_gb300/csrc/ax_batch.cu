@@ -482,11 +482,7 @@ ax_status ax_batch_setup(ax_batch **out, int B, const int64_t *E, const int *N, 
         at += E[m];
       }
     }
-    pl.sc.n_chunks = b->nblk;
-    pl.sc.cmesh = b->bmesh;
-    pl.sc.clo = b->blo;
-    pl.sc.chi = b->bhi;
-    pl.sc.pbeg = b->pbeg;
+    pl.glob_off = b->glob_off;
     e = persist::plan_build(pl, s);
     b->use_persist = e == cudaSuccess;
   }

@@ -51,6 +51,7 @@ struct Ctx {
   void *lam = nullptr;
   size_t lam_bytes = 0;
   int *wide = nullptr;  // AX_F64DW: block list of the scaled fix-up pass (int[2 + E], zeroed)
+  int *kerr = nullptr;  // AX_TF32: error word of the tensor-core AxLocal's bounded waits
   // device staging buffers for ax_local_host
   void *hx = nullptr, *hy = nullptr;
   size_t hbytes = 0;
@@ -89,6 +90,9 @@ struct AxArgs {
   // double-word precision: the context's list of element blocks whose X left
   // the kernel's direct range (int[2 + E], zero at rest; see ax_fiber.cuh)
   int *wide = nullptr;
+  // kernels with bounded waits (tensor-core AxLocal): error word, nonzero
+  // once a wait ran out (read by the context's synchronising calls)
+  int *err = nullptr;
 };
 
 // Launchers (return cudaSuccess or the launch error).

@@ -127,7 +127,7 @@ __device__ double cta_sum(double v) {
 // Not inlined: each order keeps its own register allocation (inlined into
 // one body, the nine orders' code took every register there is).
 template <int N1, int KIND, bool PCG>
-__device__ __forceinline__ void ax_tile(unsigned char *smem, const Group &g, int64_t e0, int cnt, const float *X, const float *p,
+__device__ __noinline__ void ax_tile(unsigned char *smem, const Group &g, int64_t e0, int cnt, const float *X, const float *p,
                         const gidx *gid, float *Y) {
   using Sh = fiber::Shape<N1, 1, false>;
   using Buf = fiber::FiberSmem<P, N1, KIND, 1, false>;
@@ -373,6 +373,13 @@ int plan_grid(const Plan &pl) {
 }
 
 void plan_free(Plan &pl) {
+  cudaFree(pl.cmesh_d);
+  cudaFree(pl.clo_d);
+  cudaFree(pl.chi_d);
+  cudaFree(pl.pbeg_d);
+  pl.cmesh_d = nullptr;
+  pl.clo_d = pl.chi_d = nullptr;
+  pl.pbeg_d = nullptr;
   cudaFree(pl.groups_d);
   cudaFree(pl.ax_d);
   cudaFree(pl.ax_need_d);
@@ -417,8 +424,30 @@ cudaError_t plan_build(Plan &pl, cudaStream_t s) {
       }
     }
   }
+  // vector chunks of the CG phases: kChunk global nodes, never across meshes
+  std::vector<int> cm, pb(pl.B + 1, 0);
+  std::vector<int64_t> lo, hi;
+  for (int m = 0; m < pl.B; ++m) {
+    pb[m] = (int)cm.size();
+    for (int64_t g = pl.glob_off[m]; g < pl.glob_off[m + 1]; g += kChunk) {
+      cm.push_back(m);
+      lo.push_back(g);
+      hi.push_back(std::min<int64_t>(g + kChunk, pl.glob_off[m + 1]));
+    }
+  }
+  pb[pl.B] = (int)cm.size();
   plan_free(pl);
   e = cudaMalloc(&pl.groups_d, sizeof(Group) * pl.groups.size());
+  if (e == cudaSuccess) e = cudaMalloc(&pl.cmesh_d, sizeof(int) * std::max<size_t>(1, cm.size()));
+  if (e == cudaSuccess) e = cudaMalloc(&pl.clo_d, sizeof(int64_t) * std::max<size_t>(1, lo.size()));
+  if (e == cudaSuccess) e = cudaMalloc(&pl.chi_d, sizeof(int64_t) * std::max<size_t>(1, hi.size()));
+  if (e == cudaSuccess) e = cudaMalloc(&pl.pbeg_d, sizeof(int) * pb.size());
+  if (e == cudaSuccess && !cm.empty()) {
+    e = cudaMemcpyAsync(pl.cmesh_d, cm.data(), sizeof(int) * cm.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl.clo_d, lo.data(), sizeof(int64_t) * lo.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pl.chi_d, hi.data(), sizeof(int64_t) * hi.size(), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.pbeg_d, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMalloc(&pl.ax_d, sizeof(AxItem) * std::max<size_t>(1, items.size()));
   if (e == cudaSuccess) e = cudaMalloc(&pl.ax_need_d, sizeof(int) * pl.B);
   if (e == cudaSuccess) e = cudaMalloc(&pl.ctl_d, sizeof(int) * (4 + 3 * pl.B));
@@ -431,6 +460,11 @@ cudaError_t plan_build(Plan &pl, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors go out of scope
   if (e != cudaSuccess) return e;
   pl.sc.B = pl.B;
+  pl.sc.n_chunks = (int)cm.size();
+  pl.sc.cmesh = pl.cmesh_d;
+  pl.sc.clo = pl.clo_d;
+  pl.sc.chi = pl.chi_d;
+  pl.sc.pbeg = pl.pbeg_d;
   pl.sc.groups = pl.groups_d;
   pl.sc.ax = pl.ax_d;
   pl.sc.n_ax = (int)items.size();

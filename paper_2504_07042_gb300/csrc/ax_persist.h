@@ -15,6 +15,9 @@ namespace persist {
 constexpr int kThreads = 128;  // CTA of the persistent kernel: the widest order shape for N1 <= 10
 constexpr int kMaxOrder = 9;   // orders the persistent kernel carries (N1 = 2..10)
 constexpr long long kDefaultBudgetNs = 2000000000LL;  // bound of one dependency wait: 2 s
+// global nodes per vector item of the CG phases (64 per thread): few enough
+// items that the dequeue, wait and arrival cost stays small per node
+constexpr int64_t kChunk = 8192;
 
 // One order group of the batch: a context over the union of its meshes'
 // elements (float32 geometry records), its elements at loc in the batch's
@@ -39,7 +42,7 @@ struct Sched {
   const AxItem *ax = nullptr;
   int n_ax = 0;
   const int *ax_need = nullptr;  // [B] AxLocal items per mesh
-  // vector chunks (the batched CG's reduction segmentation): chunk c covers
+  // vector chunks (kChunk global nodes, never across meshes): chunk c covers
   // global nodes [clo[c], chi[c]) of mesh cmesh[c]; mesh m owns chunks [pbeg[m], pbeg[m+1])
   int n_chunks = 0;
   const int *cmesh = nullptr;
@@ -67,6 +70,7 @@ struct Plan {
   std::vector<int> tile_blocks;          // per group: element blocks per AxLocal item (autotuned)
   std::vector<int> mesh_group;           // per mesh
   std::vector<int64_t> mesh_e0, mesh_E;  // per mesh: first element within its group, element count
+  std::vector<int64_t> glob_off;         // [B + 1] offsets of the meshes in the batch's global vector
   int grid_mult = 0;                     // CTAs = grid_mult x SMs (0: the occupancy limit)
   int sms = 0, occ = 0;
   size_t smem = 0;
@@ -74,6 +78,8 @@ struct Plan {
   Group *groups_d = nullptr;
   AxItem *ax_d = nullptr;
   int *ax_need_d = nullptr, *ctl_d = nullptr;
+  int *cmesh_d = nullptr, *pbeg_d = nullptr;
+  int64_t *clo_d = nullptr, *chi_d = nullptr;
 };
 
 // Whether a batch of these orders and this precision runs on the persistent kernel.

@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include "ax_fiber.cuh"
+#include "ax_umma.cuh"
 
 namespace ax {
 namespace tcx {
@@ -294,6 +295,18 @@ cudaError_t launch_tc_kind(const AxArgs &a, const float *Dp) {
 
 template <int MODE, int N1>
 cudaError_t launch_tc_n(const AxArgs &a, const float *Dp) {
+  if constexpr (MODE == kTF32 && N1 == 8) {
+    // order 7 in TF32: tcgen05 (tile variant 1 selects the mma.sync kernel below)
+    if (a.tile != 1) {
+      switch (a.kind) {
+        case AX_GEOM_STORED: return umma::launch_kind<AX_GEOM_STORED>(a, Dp);
+        case AX_GEOM_TRILINEAR: return umma::launch_kind<AX_GEOM_TRILINEAR>(a, Dp);
+        case AX_GEOM_PARALLELEPIPED: return umma::launch_kind<AX_GEOM_PARALLELEPIPED>(a, Dp);
+        case AX_GEOM_TRILINEAR_PARTIAL: return umma::launch_kind<AX_GEOM_TRILINEAR_PARTIAL>(a, Dp);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
   switch (a.kind) {
     case AX_GEOM_STORED: return launch_tc_kind<MODE, N1, AX_GEOM_STORED>(a, Dp);
     case AX_GEOM_TRILINEAR: return launch_tc_kind<MODE, N1, AX_GEOM_TRILINEAR>(a, Dp);

@@ -1,0 +1,332 @@
+// AxLocal with the six contractions of Algorithm 1 on the 5th-generation
+// tensor cores (tcgen05.mma kind::tf32, accumulation in tensor memory), for
+// order N = 7 (N1 = 8).
+//
+// A contraction along one direction is a [fibers x 8] by [8 x 8] product.
+// Two elements' 64 fibers of one direction make the M = 128 rows of one
+// MMA (M = 128, N = 16 with D padded by 8 zero columns, K = 8):
+//   forward    x_d[f][a] = sum_m X[f][m] D[a][m]     B = D   (row a, K = m)
+//   transposed y_d[f][m] = sum_a t_d[f][a] D[a][m]   B = D^T (row m, K = a)
+// with the fibers of direction d as rows: r-fibers (j, k), s-fibers (i, k),
+// t-fibers (i, j).  All operands are K-major in shared memory in the
+// canonical core-matrix layout without swizzle (8 rows x 16 bytes
+// contiguous, LBO between the two K halves, SBO between 8-row groups); each
+// operand buffer has its own LBO and SBO, chosen so that the threads'
+// stores into it are free of bank conflicts (the t buffer: at most 2-way).
+//
+// One CTA of 128 threads (thread = TMEM lane = row of the MMA) per tile of
+// two elements, persistent over tiles:
+//   1. X (coalesced float4 loads) into the three operand buffers, one per
+//      fiber direction; the geometry records into shared memory
+//   2. one thread issues the three forward MMAs into TMEM columns 0, 16, 32
+//      and commits them to an mbarrier
+//   3. every thread reads its rows (tcgen05.ld): thread (j,k) the x0 row
+//      over i, (i,k) the x1 row over j, (i,j) the x2 row over k; x0 and x1
+//      go through shared memory to the t-fiber owner (i,j)
+//   4. thread (i,j): per node the FP32 geometry of the fiber kernels
+//      (Algorithm 2 / 3, stored or partial) and (r,s,t) = G (x0,x1,x2)
+//   5. r, s, t into the operand buffers; the three transposed MMAs
+//   6. the three partial products are summed through shared memory by the
+//      t-fiber owners, which store Y coalesced.
+// TF32 operands: X, r, s, t are rounded to TF32 (to nearest) when staged
+// (the tensor core would otherwise drop the low mantissa bits); D is rounded
+// once.
+// Every mbarrier wait is bounded; one that runs out sets the kernel's error
+// word, and the CTA stops and frees its tensor memory.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ax_fiber.cuh"
+
+namespace ax {
+namespace umma {
+
+constexpr int kN1 = 8, kN3 = 512, kEPB = 2, kThreads = 128, kTmemCols = 64;
+// operand buffers: r (rows (j,k,e), K = i), s (rows (i,k,e), K = j), t (rows (i,j,e), K = k)
+constexpr uint32_t kLboR = 448, kSboR = 288, kLboS = 144, kSboS = 288, kLboT = 128, kSboT = 272;
+constexpr uint32_t kBytesR = 4896, kBytesS = 4592, kBytesT = 4336;
+constexpr uint32_t kLboB = 128, kSboB = 256, kBytesB = 512;  // D and D^T padded to 16 rows
+// shared memory: r, s, t buffers (r and s also carry the exchanges, 4096 bytes
+// each), B_D, B_DT, geometry records, mbarrier, TMEM address
+constexpr uint32_t kOffR = 0, kOffS = kOffR + kBytesR, kOffT = kOffS + kBytesS, kOffBD = kOffT + kBytesT,
+                   kOffBDT = kOffBD + kBytesB, kOffGeo = kOffBDT + kBytesB;
+constexpr uint32_t kSmemBytes = kOffGeo + kEPB * kVertexWords * 4 + 64;
+constexpr long long kWaitCycles = 1ll << 32;  // SM clocks (about 2 s) before a wait gives up
+
+// tcgen05.mma kind::tf32: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2), both
+// K-major, N = 16 (bits 17-22 = N >> 3), M = 128 (bits 24-28 = M >> 4)
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+// byte offset of (row, k) in a K-major no-swizzle core-matrix layout
+__host__ __device__ constexpr uint32_t cm_off(int row, int k, uint32_t lbo, uint32_t sbo) {
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 2) * lbo + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory descriptor: K-major, no swizzle, descriptor version 1
+__device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(0u));
+}
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 63u) == 63u && clock64() - t0 > kWaitCycles) return false;
+  }
+}
+// 8 float32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ float tf32_rn(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads)
+    ax_umma_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
+                   const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
+                   int *__restrict__ err) {
+  using P = fiber::Native<float>;
+  constexpr int GW = fiber::GeoWords<KIND>::value;
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char *bufR = sm + kOffR, *bufS = sm + kOffS, *bufT = sm + kOffT;
+  float *sgeo = (float *)(sm + kOffGeo);
+  uint64_t *bar = (uint64_t *)(sm + kOffGeo + kEPB * kVertexWords * 4);
+  uint32_t *tslot = (uint32_t *)(bar + 1);
+  __shared__ int abort_cta;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const float *cw = fiber::c_w + tab_off_v(kN1);
+  const float *cx = fiber::c_x + tab_off_v(kN1);
+
+  // D (rows a, K = m) and D^T (rows m, K = a), TF32, rows 8..15 zero
+  for (int q = tid; q < 2 * 16 * 8; q += kThreads) {
+    const int which = q >> 7, row = (q >> 3) & 15, k = q & 7;
+    float v = 0.0f;
+    if (row < kN1) v = tf32_rn(which == 0 ? Dp[row * kN1 + k] : Dp[k * kN1 + row]);
+    *(float *)(sm + (which == 0 ? kOffBD : kOffBDT) + cm_off(row, k, kLboB, kSboB)) = v;
+  }
+  if (tid == 0) {
+    abort_cta = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t aR = smem_u32(bufR), aS = smem_u32(bufS), aT = smem_u32(bufT);
+  const uint32_t aBD = smem_u32(sm + kOffBD), aBDT = smem_u32(sm + kOffBDT);
+  // this thread as a row of each direction: L = a + 8 b + 64 e
+  const int la = tid & 7, lb = (tid >> 3) & 7, le = tid >> 6;
+  uint32_t phase = 0;
+
+  // float4 loads need a 16-byte aligned X (element offsets are 2048-byte multiples)
+  const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  const int64_t ntile = (E + kEPB - 1) / kEPB;
+  for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const int64_t e0 = t * kEPB;
+    const int nel = (int)((E - e0) < kEPB ? (E - e0) : kEPB);
+    // 1. X into the three operand buffers (zeros beyond the last element)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int f = tid + kThreads * s;  // float4 index: i0 = 4 (f % 2), j, k, e
+      const int i0 = 4 * (f & 1), j = (f >> 1) & 7, k = (f >> 4) & 7, e = f >> 7;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < nel) {
+        if (vec) {
+          v = reinterpret_cast<const float4 *>(X + e0 * kN3)[f];
+        } else {
+          const float *src = X + e0 * kN3 + 4 * f;
+          v = make_float4(src[0], src[1], src[2], src[3]);
+        }
+      }
+      v = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));  // round, not truncate
+      *(float4 *)(bufR + cm_off(j + 8 * k + 64 * e, i0, kLboR, kSboR)) = v;
+      const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        *(float *)(bufS + cm_off(i0 + q + 8 * k + 64 * e, j, kLboS, kSboS)) = c[q];
+        *(float *)(bufT + cm_off(i0 + q + 8 * j + 64 * e, k, kLboT, kSboT)) = c[q];
+      }
+    }
+    if constexpr (GW > 0) {
+      for (int m = tid; m < nel * GW; m += kThreads) sgeo[m] = geo[e0 * GW + m];
+    }
+    proxy_fence();
+    __syncthreads();
+    // 2. forward MMAs
+    if (tid == 0 && !abort_cta) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      mma_tf32(tmem + 0, desc(aR, kLboR, kSboR), desc(aBD, kLboB, kSboB));
+      mma_tf32(tmem + 16, desc(aS, kLboS, kSboS), desc(aBD, kLboB, kSboB));
+      mma_tf32(tmem + 32, desc(aT, kLboT, kSboT), desc(aBD, kLboB, kSboB));
+      commit(smem_u32(bar));
+    }
+    // thread 0 waits for the MMAs (bounded); the others sleep in the barrier
+    if (tid == 0 && !mbar_wait(smem_u32(bar), phase)) abort_cta = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (abort_cta) {
+      if (tid == 0) mbar_wait(smem_u32(bar), phase);  // bounded: the MMAs in flight before TMEM is freed
+      break;
+    }
+    phase ^= 1u;
+    // 3. rows out of TMEM; x0 (over i) and x1 (over j) to the t-fiber owners
+    float x0[8], x1[8], x2[8];
+    tmem_ld8(tlane + 0, x0);
+    tmem_ld8(tlane + 16, x1);
+    tmem_ld8(tlane + 32, x2);
+    tmem_wait_ld();
+    float *ex0 = (float *)bufR, *ex1 = (float *)bufS;  // [e][k][j][i], float32
+    {
+      // thread as r-row (j, k) = (la, lb): x0[i] at (i, j, k); as s-row (i, k) = (la, lb): x1[j] at (i, j, k)
+      float4 *p = (float4 *)(ex0 + le * kN3 + 64 * lb + 8 * la);
+      p[0] = make_float4(x0[0], x0[1], x0[2], x0[3]);
+      p[1] = make_float4(x0[4], x0[5], x0[6], x0[7]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ex1[le * kN3 + 64 * lb + 8 * q + la] = x1[q];
+    }
+    __syncthreads();
+    // 4. geometry along the t-fiber of (i, j) = (la, lb), element le
+    float rr[8], ss[8], tt[8];
+    {
+      const bool live = le < nel;
+      const int64_t e = e0 + le;
+      fiber::Geometry<P, kN1, KIND> gm;
+      gm.template prologue<false>(sgeo + le * (GW > 0 ? GW : 1), cx, cw, la, lb,
+                                  (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * kN3 : nullptr,
+                                  (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * kN3 : nullptr, nullptr);
+#pragma unroll
+      for (int k = 0; k < kN1; ++k) {
+        const int o = le * kN3 + 64 * k + 8 * lb + la;
+        const float xv[3] = {ex0[o], ex1[o], x2[k]};
+        float o3[3] = {0.f, 0.f, 0.f};
+        if (live) gm.apply(la + lb * kN1 + k * kN1 * kN1, cx[k], cw[k], xv, o3);
+        rr[k] = tf32_rn(o3[0]);
+        ss[k] = tf32_rn(o3[1]);
+        tt[k] = tf32_rn(o3[2]);
+      }
+    }
+    __syncthreads();  // every read of the exchange buffers is done
+    // 5. r, s, t into the operand buffers; transposed MMAs
+#pragma unroll
+    for (int k = 0; k < kN1; ++k) {
+      *(float *)(bufR + cm_off(lb + 8 * k + 64 * le, la, kLboR, kSboR)) = rr[k];
+      *(float *)(bufS + cm_off(la + 8 * k + 64 * le, lb, kLboS, kSboS)) = ss[k];
+    }
+    *(float4 *)(bufT + cm_off(tid, 0, kLboT, kSboT)) = make_float4(tt[0], tt[1], tt[2], tt[3]);
+    *(float4 *)(bufT + cm_off(tid, 4, kLboT, kSboT)) = make_float4(tt[4], tt[5], tt[6], tt[7]);
+    proxy_fence();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      mma_tf32(tmem + 0, desc(aR, kLboR, kSboR), desc(aBDT, kLboB, kSboB));
+      mma_tf32(tmem + 16, desc(aS, kLboS, kSboS), desc(aBDT, kLboB, kSboB));
+      mma_tf32(tmem + 32, desc(aT, kLboT, kSboT), desc(aBDT, kLboB, kSboB));
+      commit(smem_u32(bar));
+    }
+    if (tid == 0 && !mbar_wait(smem_u32(bar), phase)) abort_cta = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (abort_cta) {
+      if (tid == 0) mbar_wait(smem_u32(bar), phase);
+      break;
+    }
+    phase ^= 1u;
+    // 6. Y = Y_r + Y_s + Y_t
+    float yr[8], ys[8], yt[8];
+    tmem_ld8(tlane + 0, yr);
+    tmem_ld8(tlane + 16, ys);
+    tmem_ld8(tlane + 32, yt);
+    tmem_wait_ld();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    {
+      float4 *p = (float4 *)(ex0 + le * kN3 + 64 * lb + 8 * la);
+      p[0] = make_float4(yr[0], yr[1], yr[2], yr[3]);
+      p[1] = make_float4(yr[4], yr[5], yr[6], yr[7]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ex1[le * kN3 + 64 * lb + 8 * q + la] = ys[q];
+    }
+    __syncthreads();
+    if (le < nel) {
+      float *ye = Y + (e0 + le) * kN3 + la + 8 * lb;
+#pragma unroll
+      for (int k = 0; k < kN1; ++k) {
+        const int o = le * kN3 + 64 * k + 8 * lb + la;
+        ye[64 * k] = ex0[o] + ex1[o] + yt[k];
+      }
+    }
+    __syncthreads();  // the next tile reuses every buffer
+  }
+  if (tid == 0 && abort_cta && err) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// Launch over a.E elements of order 7: one CTA per SM slot that the shared
+// memory, registers and tensor memory (64 of 512 columns each) allow,
+// persistent over the tiles of two elements.
+template <int KIND>
+cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
+  const int64_t ntile = (a.E + kEPB - 1) / kEPB;
+  if (ntile <= 0) return cudaSuccess;
+  static int grid_cap = 0;
+  if (!grid_cap) {
+    cudaError_t e = cudaFuncSetAttribute(ax_umma_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    int dev = 0, sms = 0, occ = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ax_umma_kernel<KIND>, kThreads, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (occ > 512 / kTmemCols) occ = 512 / kTmemCols;
+    grid_cap = (occ > 0 ? occ : 1) * sms;
+  }
+  const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
+  const int64_t grid = ntile < cap ? ntile : cap;
+  ax_umma_kernel<KIND><<<(unsigned)grid, kThreads, kSmemBytes, a.stream>>>(
+      a.E, (const float *)a.geo, (const float *)a.lam, (const float *)a.X, (float *)a.Y, Dp, a.err);
+  return cudaGetLastError();
+}
+
+}  // namespace umma
+}  // namespace ax

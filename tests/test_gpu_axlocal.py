@@ -107,7 +107,8 @@ def test_tensor_core_every_order(ax, orc, kind, prec, N):
     assert err <= TOL[prec]
 
 
-@pytest.mark.parametrize("N,prec", [(3, "fp32"), (7, "fp32"), (5, "tf32"), (7, "bf16"), (15, "f64dw"), (6, "fp32")])
+@pytest.mark.parametrize("N,prec", [(3, "fp32"), (7, "fp32"), (5, "tf32"), (7, "tf32"), (7, "bf16"), (15, "f64dw"),
+                                    (6, "fp32")])
 def test_unaligned_x_takes_word_loads(ax, N, prec):
     # X (and Y) one element past a 16-byte boundary: the kernels that read 16-byte
     # vectors from an aligned X fall back to word loads, with identical results
@@ -272,4 +273,30 @@ def test_full_size_sampled(ax, orc, kind, prec):
     idx = np.concatenate([[0, E - 1], rng.choice(E, 254, replace=False)])
     Yref, _ = orc.axlocal_vertices(V[idx], X[idx], N)
     assert _relerr(Y[idx], Yref) <= 1e-12
+    assert np.isfinite(Y).all()
+
+
+@pytest.mark.parametrize("kind", ["trilinear", "stored", "parallelepiped", "partial"])
+def test_tf32_tcgen05_full_size_sampled(ax, orc, kind):
+    # order 7 in TF32 runs on tcgen05 (TMEM accumulators): the order-7 sweep
+    # workload in the launch configuration the benchmark times, 256 sampled
+    # elements against the oracle at the TF32 tolerance; no wait ran out
+    N = 7
+    ex, ey, ez = inputs.sweep_box(N)
+    V = inputs.parallelepiped_vertices(ex, ey, ez) if kind == "parallelepiped" else \
+        inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    E = V.shape[0]
+    X = inputs.element_vectors(E, N, seed=1).astype(np.float32)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, "tf32")
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.full_like(Xd, float("nan"))
+    op.ax_local(Xd, Yd)
+    op.ax_check()
+    Y = Yd.double().cpu().numpy()
+    op.ax_destroy()
+    rng = np.random.default_rng(98)
+    idx = np.concatenate([[0, E - 1], rng.choice(E, 254, replace=False)])
+    Yref, _ = orc.axlocal_vertices(V[idx], X[idx].astype(np.float64), N)
+    assert _relerr(Y[idx], Yref) <= 4 * 2.0 ** -11
     assert np.isfinite(Y).all()
