@@ -47,6 +47,7 @@ namespace persist {
 
 using P = fiber::Native<float>;
 constexpr int kS = 16;  // per-mesh scalars, same slots as the batched CG of ax_batch.cu
+constexpr int kU = 4;   // gather-dot: nodes per thread whose gathers are in flight together
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -173,12 +174,33 @@ __device__ void run_gd(const Sched &sc, const Vecs &v, int c) {
   const bool done = __ldcg(&v.S[m * kS + 6]) != 0.0;
   float d = 0.0f;
   if (!done) {
-    for (int64_t g = sc.clo[c] + threadIdx.x; g < sc.chi[c]; g += kThreads) {
-      float s = 0.0f;
-      for (gidx q = v.off[g]; q < v.off[g + 1]; ++q) s += __ldcg(&v.Yl[v.idx[q]]);
-      if (v.mask && v.mask[g]) s = 0.0f;
-      v.w[g] = s;
-      d += v.p[g] * s;
+    // kU nodes per thread at a time, their gathers issued together (a hexahedral
+    // node has at most 8 local copies; more are summed by the tail loop)
+    const int64_t hi = sc.chi[c];
+    for (int64_t g0 = sc.clo[c] + threadIdx.x; g0 < hi; g0 += kU * kThreads) {
+      gidx b[kU], n[kU];
+      float s[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t g = g0 + u * kThreads;
+        b[u] = g < hi ? v.off[g] : 0;
+        n[u] = g < hi ? v.off[g + 1] - b[u] : 0;
+        s[u] = 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (q < n[u]) s[u] += __ldcg(&v.Yl[v.idx[b[u] + q]]);
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t g = g0 + u * kThreads;
+        if (g >= hi) break;
+        for (int q = 8; q < n[u]; ++q) s[u] += __ldcg(&v.Yl[v.idx[b[u] + q]]);
+        if (v.mask && v.mask[g]) s[u] = 0.0f;
+        v.w[g] = s[u];
+        d += v.p[g] * s[u];
+      }
     }
   }
   const double ds = cta_sum((double)d);
@@ -207,6 +229,7 @@ __device__ void run_up(const Sched &sc, const Vecs &v, int c) {
   float rz = 0.0f, rr = 0.0f;
   if (!done) {
     const float alpha = (float)__ldcg(&v.S[m * kS + 10]);
+#pragma unroll 4
     for (int64_t g = sc.clo[c] + threadIdx.x; g < sc.chi[c]; g += kThreads) {
       const float rg = v.r[g] - alpha * __ldcg(&v.w[g]);
       float zg = v.inv ? rg * v.inv[g] : rg;
@@ -261,6 +284,7 @@ __device__ void run_di(const Sched &sc, const Vecs &v, int c) {
   if (!cta_wait(&sc.cnt[2 * sc.B + m], need + 1, sc)) return;
   if (__ldcg(&v.S[m * kS + 6]) != 0.0) return;
   const float beta = (float)__ldcg(&v.S[m * kS + 11]);
+#pragma unroll 4
   for (int64_t g = sc.clo[c] + threadIdx.x; g < sc.chi[c]; g += kThreads) v.p[g] = __ldcg(&v.z[g]) + beta * v.p[g];
 }
 

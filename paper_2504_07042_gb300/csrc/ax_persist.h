@@ -15,9 +15,9 @@ namespace persist {
 constexpr int kThreads = 128;  // CTA of the persistent kernel: the widest order shape for N1 <= 10
 constexpr int kMaxOrder = 9;   // orders the persistent kernel carries (N1 = 2..10)
 constexpr long long kDefaultBudgetNs = 2000000000LL;  // bound of one dependency wait: 2 s
-// global nodes per vector item of the CG phases (64 per thread): few enough
+// global nodes per vector item of the CG phases (32 per thread): few enough
 // items that the dequeue, wait and arrival cost stays small per node
-constexpr int64_t kChunk = 8192;
+constexpr int64_t kChunk = 4096;
 
 // One order group of the batch: a context over the union of its meshes'
 // elements (float32 geometry records), its elements at loc in the batch's

@@ -47,7 +47,11 @@ namespace umma {
 constexpr int kN1 = 8, kN3 = 512, kEPB = 2, kThreads = 128, kTmemCols = 64;
 // operand buffers: r (rows (j,k,e), K = i), s (rows (i,k,e), K = j), t (rows (i,j,e), K = k)
 constexpr uint32_t kLboR = 448, kSboR = 288, kLboS = 144, kSboS = 288, kLboT = 128, kSboT = 272;
-constexpr uint32_t kBytesR = 4896, kBytesS = 4592, kBytesT = 4336;
+constexpr uint32_t kBytesR = 4896, kBytesS = 4608, kBytesT = 4336;
+// exchange buffers (aliasing r and s): [e][k][j][i] float32 with pitches 576,
+// 72, 8, 1 floats (the k pitch 72 = 8 mod 32 keeps the stride-8 row writes
+// and the t-fiber reads free of bank conflicts)
+constexpr int kXe = 576, kXk = 72;
 constexpr uint32_t kLboB = 128, kSboB = 256, kBytesB = 512;  // D and D^T padded to 16 rows
 // shared memory: r, s, t buffers (r and s also carry the exchanges, 4096 bytes
 // each), B_D, B_DT, geometry records, mbarrier, TMEM address
@@ -111,7 +115,7 @@ __device__ __forceinline__ float tf32_rn(float v) {
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
     ax_umma_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
                    const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
                    int *__restrict__ err) {
@@ -159,23 +163,36 @@ __global__ void __launch_bounds__(kThreads)
   // float4 loads need a 16-byte aligned X (element offsets are 2048-byte multiples)
   const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   const int64_t ntile = (E + kEPB - 1) / kEPB;
+  // X of a tile: two float4 per thread (float4 index f = i0/4 + 2 j + 16 k + 128 e),
+  // loaded one tile ahead so that the loads overlap the previous tile's work
+  auto load_x = [&](int64_t tt, float4 xv[2]) {
+    const int64_t b0 = tt * kEPB;
+    const int nl = (int)((E - b0) < kEPB ? (E - b0) : kEPB);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int f = tid + kThreads * s;
+      xv[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (tt < ntile && (f >> 7) < nl) {
+        if (vec) {
+          xv[s] = reinterpret_cast<const float4 *>(X + b0 * kN3)[f];
+        } else {
+          const float *src = X + b0 * kN3 + 4 * f;
+          xv[s] = make_float4(src[0], src[1], src[2], src[3]);
+        }
+      }
+    }
+  };
+  float4 xnext[2];
+  load_x(blockIdx.x, xnext);
   for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
     const int64_t e0 = t * kEPB;
     const int nel = (int)((E - e0) < kEPB ? (E - e0) : kEPB);
     // 1. X into the three operand buffers (zeros beyond the last element)
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const int f = tid + kThreads * s;  // float4 index: i0 = 4 (f % 2), j, k, e
+      const int f = tid + kThreads * s;
       const int i0 = 4 * (f & 1), j = (f >> 1) & 7, k = (f >> 4) & 7, e = f >> 7;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e < nel) {
-        if (vec) {
-          v = reinterpret_cast<const float4 *>(X + e0 * kN3)[f];
-        } else {
-          const float *src = X + e0 * kN3 + 4 * f;
-          v = make_float4(src[0], src[1], src[2], src[3]);
-        }
-      }
+      float4 v = xnext[s];
       v = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));  // round, not truncate
       *(float4 *)(bufR + cm_off(j + 8 * k + 64 * e, i0, kLboR, kSboR)) = v;
       const float c[4] = {v.x, v.y, v.z, v.w};
@@ -188,6 +205,7 @@ __global__ void __launch_bounds__(kThreads)
     if constexpr (GW > 0) {
       for (int m = tid; m < nel * GW; m += kThreads) sgeo[m] = geo[e0 * GW + m];
     }
+    load_x(t + gridDim.x, xnext);  // the next tile's X, in flight meanwhile
     proxy_fence();
     __syncthreads();
     // 2. forward MMAs
@@ -213,15 +231,21 @@ __global__ void __launch_bounds__(kThreads)
     tmem_ld8(tlane + 16, x1);
     tmem_ld8(tlane + 32, x2);
     tmem_wait_ld();
-    float *ex0 = (float *)bufR, *ex1 = (float *)bufS;  // [e][k][j][i], float32
-    {
-      // thread as r-row (j, k) = (la, lb): x0[i] at (i, j, k); as s-row (i, k) = (la, lb): x1[j] at (i, j, k)
-      float4 *p = (float4 *)(ex0 + le * kN3 + 64 * lb + 8 * la);
-      p[0] = make_float4(x0[0], x0[1], x0[2], x0[3]);
-      p[1] = make_float4(x0[4], x0[5], x0[6], x0[7]);
+    float *ex0 = (float *)bufR, *ex1 = (float *)bufS;  // [e][k][j][i], pitches kXe, kXk, 8, 1
+    const int xrow = le * kXe + kXk * lb + 8 * la;   // as r-row (j, k) = (la, lb): x0[i] at (i, j, k)
+    const int xcol = le * kXe + kXk * lb + la;       // as s-row (i, k) = (la, lb): x1[j] at (i, j, k)
+    const int xown = le * kXe + 8 * lb + la;         // as t-fiber owner (i, j) = (la, lb): + kXk k
+    // the two 16-byte halves of a row in an order that differs between lanes
+    // la and la + 4 (they share banks otherwise)
+    auto put_row = [&](float *b, const float v[8]) {
+      const int h = (la >> 2) & 1;
+      float4 *p = (float4 *)(b + xrow);
+      p[h] = h ? make_float4(v[4], v[5], v[6], v[7]) : make_float4(v[0], v[1], v[2], v[3]);
+      p[h ^ 1] = h ? make_float4(v[0], v[1], v[2], v[3]) : make_float4(v[4], v[5], v[6], v[7]);
+    };
+    put_row(ex0, x0);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) ex1[le * kN3 + 64 * lb + 8 * q + la] = x1[q];
-    }
+    for (int q = 0; q < 8; ++q) ex1[xcol + 8 * q] = x1[q];
     __syncthreads();
     // 4. geometry along the t-fiber of (i, j) = (la, lb), element le
     float rr[8], ss[8], tt[8];
@@ -234,7 +258,7 @@ __global__ void __launch_bounds__(kThreads)
                                   (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * kN3 : nullptr, nullptr);
 #pragma unroll
       for (int k = 0; k < kN1; ++k) {
-        const int o = le * kN3 + 64 * k + 8 * lb + la;
+        const int o = xown + kXk * k;
         const float xv[3] = {ex0[o], ex1[o], x2[k]};
         float o3[3] = {0.f, 0.f, 0.f};
         if (live) gm.apply(la + lb * kN1 + k * kN1 * kN1, cx[k], cw[k], xv, o3);
@@ -277,19 +301,15 @@ __global__ void __launch_bounds__(kThreads)
     tmem_ld8(tlane + 32, yt);
     tmem_wait_ld();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    {
-      float4 *p = (float4 *)(ex0 + le * kN3 + 64 * lb + 8 * la);
-      p[0] = make_float4(yr[0], yr[1], yr[2], yr[3]);
-      p[1] = make_float4(yr[4], yr[5], yr[6], yr[7]);
+    put_row(ex0, yr);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) ex1[le * kN3 + 64 * lb + 8 * q + la] = ys[q];
-    }
+    for (int q = 0; q < 8; ++q) ex1[xcol + 8 * q] = ys[q];
     __syncthreads();
     if (le < nel) {
       float *ye = Y + (e0 + le) * kN3 + la + 8 * lb;
 #pragma unroll
       for (int k = 0; k < kN1; ++k) {
-        const int o = le * kN3 + 64 * k + 8 * lb + la;
+        const int o = xown + kXk * k;
         ye[64 * k] = ex0[o] + ex1[o] + yt[k];
       }
     }
@@ -302,9 +322,9 @@ __global__ void __launch_bounds__(kThreads)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// Launch over a.E elements of order 7: one CTA per SM slot that the shared
-// memory, registers and tensor memory (64 of 512 columns each) allow,
-// persistent over the tiles of two elements.
+// Launch over a.E elements of order 7: eight CTAs per SM (tensor memory: 64
+// of 512 columns each; 61 registers and 16 KB of shared memory also allow
+// eight), persistent over the tiles of two elements.
 template <int KIND>
 cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
   const int64_t ntile = (a.E + kEPB - 1) / kEPB;
@@ -313,13 +333,11 @@ cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
   if (!grid_cap) {
     cudaError_t e = cudaFuncSetAttribute(ax_umma_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ax_umma_kernel<KIND>, kThreads, kSmemBytes);
     if (e != cudaSuccess) return e;
-    if (occ > 512 / kTmemCols) occ = 512 / kTmemCols;
-    grid_cap = (occ > 0 ? occ : 1) * sms;
+    grid_cap = (512 / kTmemCols) * sms;
   }
   const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
   const int64_t grid = ntile < cap ? ntile : cap;
