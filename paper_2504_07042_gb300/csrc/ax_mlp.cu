@@ -198,6 +198,7 @@ enum LpScalar {
   kBeta = 11, kBestRr = 12, kBestIt = 13, kLearnOff = 14, kMlpSkip = 15, kPatience = 16, kLpScalars = 24
 };
 constexpr int kLpBlocks = 1024;
+constexpr int kLpU = 4;  // gathers: nodes per thread whose loads are in flight together
 
 __global__ void __launch_bounds__(red::kThreads)
     lp_init(int64_t n, const double *__restrict__ b, const double *__restrict__ w, double *__restrict__ bm,
@@ -259,12 +260,33 @@ __global__ void __launch_bounds__(red::kThreads)
               double *__restrict__ part, unsigned *__restrict__ cnt, double *__restrict__ S) {
   if (S[kDone] != 0.0) return;
   double d = 0.0;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
-    if (mask && mask[g]) s = 0.0;
-    w[g] = s;
-    d += p[g] * s;
+  // kLpU nodes per thread at a time: their CSR gathers are in flight together
+  // (a hexahedral node has at most 8 local copies; more go to the tail loop)
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g0 < n; g0 += kLpU * step) {
+    gidx b[kLpU], c[kLpU];
+    double sv[kLpU];
+#pragma unroll
+    for (int u = 0; u < kLpU; ++u) {
+      const int64_t g = g0 + u * step;
+      b[u] = g < n ? off[g] : 0;
+      c[u] = g < n ? off[g + 1] - b[u] : 0;
+      sv[u] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int u = 0; u < kLpU; ++u)
+        if (q < c[u]) sv[u] += Y[idx[b[u] + q]];
+#pragma unroll
+    for (int u = 0; u < kLpU; ++u) {
+      const int64_t g = g0 + u * step;
+      if (g >= n) break;
+      for (int q = 8; q < c[u]; ++q) sv[u] += Y[idx[b[u] + q]];
+      if (mask && mask[g]) sv[u] = 0.0;
+      w[g] = sv[u];
+      d += p[g] * sv[u];
+    }
   }
   red::block_reduce_store(d, part + blockIdx.x);
   if (!red::arrive_last(cnt)) return;
@@ -337,24 +359,45 @@ __global__ void __launch_bounds__(red::kThreads)
   if (S[kDone] != 0.0) return;
   const bool learned = S[kMlpSkip] == 0.0;
   double rz = 0.0, wz = 0.0;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    const double rg = r[g];
-    // the averaged correction in float: omega / multiplicity from a table
-    // (no int -> float conversion or division on the slow pipes)
-    float sc = 0.0f;
-    if (learned && !(mask && mask[g])) {
-      const gidx q0 = off[g], q1 = off[g + 1];
-      for (gidx q = q0; q < q1; ++q) {
-        const gidx l = idx[q];
-        sc += Y[l] * scale[l >> 9];  // 512 nodes per element at N = 7
-      }
-      const int k = q1 - q0;
-      sc *= omega * (k < kRcpTable ? c_rcp[k] : __frcp_rn((float)k));
+  // kLpU nodes per thread at a time (their gathers in flight together); the
+  // averaged correction in float: omega / multiplicity from a table (no
+  // int -> float conversion or division on the slow pipes)
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g0 < n; g0 += kLpU * step) {
+    gidx b[kLpU], c[kLpU];
+    float sc[kLpU];
+#pragma unroll
+    for (int u = 0; u < kLpU; ++u) {
+      const int64_t g = g0 + u * step;
+      const bool on = g < n && learned && !(mask && mask[g]);
+      b[u] = on ? off[g] : 0;
+      c[u] = on ? off[g + 1] - b[u] : 0;
+      sc[u] = 0.0f;
     }
-    const double zg = fma(dinv[g], rg, (double)sc);
-    z[g] = zg;
-    rz += rg * zg;
-    wz += w[g] * zg;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int u = 0; u < kLpU; ++u)
+        if (q < c[u]) {
+          const gidx l = idx[b[u] + q];
+          sc[u] += Y[l] * scale[l >> 9];  // 512 nodes per element at N = 7
+        }
+#pragma unroll
+    for (int u = 0; u < kLpU; ++u) {
+      const int64_t g = g0 + u * step;
+      if (g >= n) break;
+      for (int q = 8; q < c[u]; ++q) {
+        const gidx l = idx[b[u] + q];
+        sc[u] += Y[l] * scale[l >> 9];
+      }
+      const int k = c[u];
+      if (k > 0) sc[u] *= omega * (k < kRcpTable ? c_rcp[k] : __frcp_rn((float)k));
+      const double rg = r[g];
+      const double zg = fma(dinv[g], rg, (double)sc[u]);
+      z[g] = zg;
+      rz += rg * zg;
+      wz += w[g] * zg;
+    }
   }
   red::block_reduce_store(rz, part + blockIdx.x);
   __syncthreads();

@@ -44,21 +44,36 @@
 namespace ax {
 namespace umma {
 
-constexpr int kN1 = 8, kN3 = 512, kEPB = 2, kThreads = 128, kTmemCols = 64;
-// operand buffers: r (rows (j,k,e), K = i), s (rows (i,k,e), K = j), t (rows (i,j,e), K = k)
-constexpr uint32_t kLboR = 448, kSboR = 288, kLboS = 144, kSboS = 288, kLboT = 128, kSboT = 272;
-constexpr uint32_t kBytesR = 4896, kBytesS = 4608, kBytesT = 4336;
-// exchange buffers (aliasing r and s): [e][k][j][i] float32 with pitches 576,
-// 72, 8, 1 floats (the k pitch 72 = 8 mod 32 keeps the stride-8 row writes
-// and the t-fiber reads free of bank conflicts)
+constexpr int kN1 = 8, kN3 = 512, kEPB = 2, kThreads = 128, kTmemCols = 32;
+// operand buffers: r (rows (j,k,e), K = i), s (rows (i,k,e), K = j), t (rows (i,j,e), K = k);
+// strides from a search over the threads' store patterns: r free of bank
+// conflicts, s and t at most 2-way (a dense r, also 2-way, measured 3% slower)
+constexpr uint32_t kLboR = 448, kSboR = 288, kLboS = 128, kSboS = 272, kLboT = 128, kSboT = 272;
+constexpr uint32_t kBytesR = 4896, kBytesS = 4336, kBytesT = 4336;
+// exchange buffers (x0, x1, then Y_r, Y_s): [e][k][j][i] float32 with pitches
+// 576, 72, 8, 1 floats (the k pitch 72 = 8 mod 32 keeps the stride-8 row
+// writes and the t-fiber reads free of bank conflicts); apart from the
+// operand buffers, so that staging a tile's operands needs no barrier after
+// the reads of the previous exchange
 constexpr int kXe = 576, kXk = 72;
-constexpr uint32_t kLboB = 128, kSboB = 256, kBytesB = 512;  // D and D^T padded to 16 rows
-// shared memory: r, s, t buffers (r and s also carry the exchanges, 4096 bytes
-// each), B_D, B_DT, geometry records, mbarrier, TMEM address
-constexpr uint32_t kOffR = 0, kOffS = kOffR + kBytesR, kOffT = kOffS + kBytesS, kOffBD = kOffT + kBytesT,
-                   kOffBDT = kOffBD + kBytesB, kOffGeo = kOffBDT + kBytesB;
+constexpr uint32_t kBytesX = 2 * kXe * 4;
+// D and D^T, each in a 24-row B buffer (rows 8..15 hold it, the rest zero):
+// the 16-row descriptor window starting at row 8 puts a product in columns
+// 0-7 of its 16-column accumulator, the window starting at row 0 in columns
+// 8-15.  So the r and s products share one accumulator (x0 | x1, then
+// Y_r | Y_s) and t has the next: 32 TMEM columns per CTA
+constexpr uint32_t kLboB = 128, kSboB = 256, kBytesB = 768;
+// shared memory: r, s, t operand buffers, the two exchange buffers, the D
+// and D^T B buffers, geometry records, mbarrier, TMEM address
+constexpr uint32_t kOffR = 0, kOffS = kOffR + kBytesR, kOffT = kOffS + kBytesS, kOffX0 = kOffT + kBytesT,
+                   kOffX1 = kOffX0 + kBytesX, kOffBD = kOffX1 + kBytesX, kOffBDT = kOffBD + kBytesB,
+                   kOffGeo = kOffBDT + kBytesB;
 constexpr uint32_t kSmemBytes = kOffGeo + kEPB * kVertexWords * 4 + 64;
 constexpr long long kWaitCycles = 1ll << 32;  // SM clocks (about 2 s) before a wait gives up
+// resident CTAs per SM: the shared memory (about 25 KB each) allows eight;
+// the registers are sized for them (at most 64 per thread) and the tensor
+// memory would allow 512 / 32 = 16
+constexpr int kCtasPerSm = 8;
 
 // tcgen05.mma kind::tf32: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2), both
 // K-major, N = 16 (bits 17-22 = N >> 3), M = 128 (bits 24-28 = M >> 4)
@@ -75,11 +90,11 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t 
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(0u));
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate));
 }
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
@@ -96,6 +111,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (ok) return true;
     if ((it & 63u) == 63u && clock64() - t0 > kWaitCycles) return false;
   }
+}
+// 16 float32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 // 8 float32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
@@ -115,7 +141,7 @@ __device__ __forceinline__ float tf32_rn(float v) {
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
     ax_umma_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
                    const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
                    int *__restrict__ err) {
@@ -131,11 +157,12 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
   const float *cw = fiber::c_w + tab_off_v(kN1);
   const float *cx = fiber::c_x + tab_off_v(kN1);
 
-  // D (rows a, K = m) and D^T (rows m, K = a), TF32, rows 8..15 zero
-  for (int q = tid; q < 2 * 16 * 8; q += kThreads) {
-    const int which = q >> 7, row = (q >> 3) & 15, k = q & 7;
+  // D (rows a, K = m) and D^T (rows m, K = a), TF32, at rows 8..15 of their
+  // 24-row buffers, zero elsewhere
+  for (int q = tid; q < 2 * 24 * 8; q += kThreads) {
+    const int which = q / 192, row = (q % 192) >> 3, k = q & 7, a = row - 8;
     float v = 0.0f;
-    if (row < kN1) v = tf32_rn(which == 0 ? Dp[row * kN1 + k] : Dp[k * kN1 + row]);
+    if (a >= 0 && a < kN1) v = tf32_rn(which == 0 ? Dp[a * kN1 + k] : Dp[k * kN1 + a]);
     *(float *)(sm + (which == 0 ? kOffBD : kOffBDT) + cm_off(row, k, kLboB, kSboB)) = v;
   }
   if (tid == 0) {
@@ -211,9 +238,9 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
     // 2. forward MMAs
     if (tid == 0 && !abort_cta) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      mma_tf32(tmem + 0, desc(aR, kLboR, kSboR), desc(aBD, kLboB, kSboB));
-      mma_tf32(tmem + 16, desc(aS, kLboS, kSboS), desc(aBD, kLboB, kSboB));
-      mma_tf32(tmem + 32, desc(aT, kLboT, kSboT), desc(aBD, kLboB, kSboB));
+      mma_tf32(tmem, desc(aR, kLboR, kSboR), desc(aBD + kSboB, kLboB, kSboB), 0u);
+      mma_tf32(tmem, desc(aS, kLboS, kSboS), desc(aBD, kLboB, kSboB), 1u);
+      mma_tf32(tmem + 16, desc(aT, kLboT, kSboT), desc(aBD + kSboB, kLboB, kSboB), 0u);
       commit(smem_u32(bar));
     }
     // thread 0 waits for the MMAs (bounded); the others sleep in the barrier
@@ -226,12 +253,12 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
     }
     phase ^= 1u;
     // 3. rows out of TMEM; x0 (over i) and x1 (over j) to the t-fiber owners
-    float x0[8], x1[8], x2[8];
-    tmem_ld8(tlane + 0, x0);
-    tmem_ld8(tlane + 16, x1);
-    tmem_ld8(tlane + 32, x2);
+    float x01[16], x2[8];  // x0 in columns 0-7, x1 in 8-15, x2 in 16-23
+    tmem_ld16(tlane + 0, x01);
+    tmem_ld8(tlane + 16, x2);
     tmem_wait_ld();
-    float *ex0 = (float *)bufR, *ex1 = (float *)bufS;  // [e][k][j][i], pitches kXe, kXk, 8, 1
+    const float *x0 = x01, *x1 = x01 + 8;
+    float *ex0 = (float *)(sm + kOffX0), *ex1 = (float *)(sm + kOffX1);  // [e][k][j][i]
     const int xrow = le * kXe + kXk * lb + 8 * la;   // as r-row (j, k) = (la, lb): x0[i] at (i, j, k)
     const int xcol = le * kXe + kXk * lb + la;       // as s-row (i, k) = (la, lb): x1[j] at (i, j, k)
     const int xown = le * kXe + 8 * lb + la;         // as t-fiber owner (i, j) = (la, lb): + kXk k
@@ -248,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
     for (int q = 0; q < 8; ++q) ex1[xcol + 8 * q] = x1[q];
     __syncthreads();
     // 4. geometry along the t-fiber of (i, j) = (la, lb), element le
-    float rr[8], ss[8], tt[8];
+    float tt[8];
     {
       const bool live = le < nel;
       const int64_t e = e0 + le;
@@ -262,17 +289,12 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
         const float xv[3] = {ex0[o], ex1[o], x2[k]};
         float o3[3] = {0.f, 0.f, 0.f};
         if (live) gm.apply(la + lb * kN1 + k * kN1 * kN1, cx[k], cw[k], xv, o3);
-        rr[k] = tf32_rn(o3[0]);
-        ss[k] = tf32_rn(o3[1]);
+        // 5. r, s into their operand buffers at once (the forward MMAs are
+        // done and the exchange buffers are apart), t after the loop
+        *(float *)(bufR + cm_off(lb + 8 * k + 64 * le, la, kLboR, kSboR)) = tf32_rn(o3[0]);
+        *(float *)(bufS + cm_off(la + 8 * k + 64 * le, lb, kLboS, kSboS)) = tf32_rn(o3[1]);
         tt[k] = tf32_rn(o3[2]);
       }
-    }
-    __syncthreads();  // every read of the exchange buffers is done
-    // 5. r, s, t into the operand buffers; transposed MMAs
-#pragma unroll
-    for (int k = 0; k < kN1; ++k) {
-      *(float *)(bufR + cm_off(lb + 8 * k + 64 * le, la, kLboR, kSboR)) = rr[k];
-      *(float *)(bufS + cm_off(la + 8 * k + 64 * le, lb, kLboS, kSboS)) = ss[k];
     }
     *(float4 *)(bufT + cm_off(tid, 0, kLboT, kSboT)) = make_float4(tt[0], tt[1], tt[2], tt[3]);
     *(float4 *)(bufT + cm_off(tid, 4, kLboT, kSboT)) = make_float4(tt[4], tt[5], tt[6], tt[7]);
@@ -281,9 +303,9 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      mma_tf32(tmem + 0, desc(aR, kLboR, kSboR), desc(aBDT, kLboB, kSboB));
-      mma_tf32(tmem + 16, desc(aS, kLboS, kSboS), desc(aBDT, kLboB, kSboB));
-      mma_tf32(tmem + 32, desc(aT, kLboT, kSboT), desc(aBDT, kLboB, kSboB));
+      mma_tf32(tmem, desc(aR, kLboR, kSboR), desc(aBDT + kSboB, kLboB, kSboB), 0u);
+      mma_tf32(tmem, desc(aS, kLboS, kSboS), desc(aBDT, kLboB, kSboB), 1u);
+      mma_tf32(tmem + 16, desc(aT, kLboT, kSboT), desc(aBDT + kSboB, kLboB, kSboB), 0u);
       commit(smem_u32(bar));
     }
     if (tid == 0 && !mbar_wait(smem_u32(bar), phase)) abort_cta = 1;
@@ -295,11 +317,11 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
     }
     phase ^= 1u;
     // 6. Y = Y_r + Y_s + Y_t
-    float yr[8], ys[8], yt[8];
-    tmem_ld8(tlane + 0, yr);
-    tmem_ld8(tlane + 16, ys);
-    tmem_ld8(tlane + 32, yt);
+    float yrs[16], yt[8];  // Y_r in columns 0-7, Y_s in 8-15, Y_t in 16-23
+    tmem_ld16(tlane + 0, yrs);
+    tmem_ld8(tlane + 16, yt);
     tmem_wait_ld();
+    const float *yr = yrs, *ys = yrs + 8;
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     put_row(ex0, yr);
 #pragma unroll
@@ -313,7 +335,8 @@ __global__ void __launch_bounds__(kThreads, 512 / kTmemCols)
         ye[64 * k] = ex0[o] + ex1[o] + yt[k];
       }
     }
-    __syncthreads();  // the next tile reuses every buffer
+    // no barrier here: the next tile writes the operand buffers (free since
+    // the MMA wait) and its exchange only after two more barriers
   }
   if (tid == 0 && abort_cta && err) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -337,7 +360,7 @@ cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    grid_cap = (512 / kTmemCols) * sms;
+    grid_cap = kCtasPerSm * sms;
   }
   const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
   const int64_t grid = ntile < cap ? ntile : cap;
