@@ -45,10 +45,10 @@ FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (meas
 # sources hash to the recorded value (else reported as null).
 # DRAM traffic per launch of the headline kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 32^3-element case of
-# the same kernel (profiles/ax_dw_trilinear_n7_e32768_full.md), scaled by
+# the same kernel (profiles/ax_dw_trilinear_n7_e32768_traffic.md), scaled by
 # elements to the 64x64x32 workload (traffic grows with the element count);
 # valid while the kernel's sources hash to "src".
-TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.567552e6 + 90.682112e6), "src": "c79c362ef5553bda"}}
+TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.582656e6 + 90.026752e6), "src": "61cfaa98bde5ac6b"}}
 
 
 # the sources that define the headline kernel (double-word AxLocal, N = 7)
