@@ -198,7 +198,10 @@ enum LpScalar {
   kBeta = 11, kBestRr = 12, kBestIt = 13, kLearnOff = 14, kMlpSkip = 15, kPatience = 16, kLpScalars = 24
 };
 constexpr int kLpBlocks = 1024;
-constexpr int kLpU = 4;  // gathers: nodes per thread whose loads are in flight together
+// lp_precond: nodes per thread whose gathers are in flight together (measured
+// 248 -> 213 us per launch at 32^3 elements; the same unrolling made lp_gather,
+// which gathers float64, slower: 136 -> 227 us, so it keeps the plain loop)
+constexpr int kLpU = 4;
 
 __global__ void __launch_bounds__(red::kThreads)
     lp_init(int64_t n, const double *__restrict__ b, const double *__restrict__ w, double *__restrict__ bm,
@@ -260,33 +263,12 @@ __global__ void __launch_bounds__(red::kThreads)
               double *__restrict__ part, unsigned *__restrict__ cnt, double *__restrict__ S) {
   if (S[kDone] != 0.0) return;
   double d = 0.0;
-  // kLpU nodes per thread at a time: their CSR gathers are in flight together
-  // (a hexahedral node has at most 8 local copies; more go to the tail loop)
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g0 < n; g0 += kLpU * step) {
-    gidx b[kLpU], c[kLpU];
-    double sv[kLpU];
-#pragma unroll
-    for (int u = 0; u < kLpU; ++u) {
-      const int64_t g = g0 + u * step;
-      b[u] = g < n ? off[g] : 0;
-      c[u] = g < n ? off[g + 1] - b[u] : 0;
-      sv[u] = 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-#pragma unroll
-      for (int u = 0; u < kLpU; ++u)
-        if (q < c[u]) sv[u] += Y[idx[b[u] + q]];
-#pragma unroll
-    for (int u = 0; u < kLpU; ++u) {
-      const int64_t g = g0 + u * step;
-      if (g >= n) break;
-      for (int q = 8; q < c[u]; ++q) sv[u] += Y[idx[b[u] + q]];
-      if (mask && mask[g]) sv[u] = 0.0;
-      w[g] = sv[u];
-      d += p[g] * sv[u];
-    }
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
+    if (mask && mask[g]) s = 0.0;
+    w[g] = s;
+    d += p[g] * s;
   }
   red::block_reduce_store(d, part + blockIdx.x);
   if (!red::arrive_last(cnt)) return;
