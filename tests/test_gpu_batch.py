@@ -266,3 +266,36 @@ def test_persistent_unsupported(ax):
     with pytest.raises(ax.AxError) as ei:
         bt.ax_batch_set_persistent(True)
     assert ei.value.status == ax.AX_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kind", ["trilinear", "partial"])
+def test_persistent_every_order(ax, orc, kind):
+    # one batch with every order the persistent kernel carries (N = 1..9,
+    # N1 = 2..10: the CTA's idle threads and each order's shape), one launch
+    spec = [(2, 2, 2, N) for N in (9, 1, 8, 2, 7, 3, 6, 4, 5)] + [(2, 2, 3, 9), (3, 2, 2, 2)]
+    meshes = []
+    for s, (ex, ey, ez, N) in enumerate(spec):
+        V = inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=40 + s)
+        gid, ng = inputs.box_global_ids(ex, ey, ez, N)
+        meshes.append((V, N, gid, ng, inputs.box_boundary_mask(ex, ey, ez, N)))
+    bt = ax.AxBatch(_dev(meshes), kind, "fp32")
+    assert bt.ax_batch_info()["local_launches"] == 1
+    X = torch.from_numpy(np.random.default_rng(73).uniform(-1, 1, bt.n_local)).to(DEV, torch.float32)
+    Y = torch.full_like(X, float("nan"))
+    bt.ax_batch_local(X, Y)
+    Xh, Yh = X.double().cpu().numpy(), Y.double().cpu().numpy()
+    for m, (V, N, gid, ng, mask) in enumerate(meshes):
+        n3 = (N + 1) ** 3
+        lo = bt.local_offsets[m]
+        Yref, _ = orc.axlocal_vertices(V, Xh[lo:lo + V.shape[0] * n3].reshape(V.shape[0], n3), N)
+        err = np.max(np.abs(Yh[lo:lo + V.shape[0] * n3].reshape(V.shape[0], n3) - Yref)) / np.max(np.abs(Yref))
+        assert err <= TOL["fp32"], (m, N, err)
+    bvec, xref = _c4_rhs(orc, bt, meshes)
+    bd = torch.from_numpy(bvec).to(DEV, torch.float32)
+    x = torch.zeros_like(bd)
+    it, rr, st = bt.ax_batch_pcg(bd, x, rtol=1e-5, maxit=5000, graph=1)
+    assert st == ax.AX_OK
+    xh = x.double().cpu().numpy()
+    for m in range(bt.B):
+        a, b = bt.global_offsets[m], bt.global_offsets[m + 1]
+        assert np.max(np.abs(xh[a:b] - xref[m])) <= 1e-4 * np.max(np.abs(xref[m])), m
