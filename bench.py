@@ -48,7 +48,7 @@ FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (meas
 # the same kernel (profiles/ax_dw_trilinear_n7_e32768_traffic.md), scaled by
 # elements to the 64x64x32 workload (traffic grows with the element count);
 # valid while the kernel's sources hash to "src".
-TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.582656e6 + 90.026752e6), "src": "61cfaa98bde5ac6b"}}
+TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.570368e6 + 90.049280e6), "src": "c10eb5e2ac9276e6"}}
 
 
 # the sources that define the headline kernel (double-word AxLocal, N = 7)
@@ -122,6 +122,40 @@ class Clocks:
         load = sorted(sm)[len(sm) // 4:] or sm  # drop the idle head of the record
         return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(rows)}
+
+
+def _host_link(torch, Xh, Yh, X, Y, reps=5):
+    """Copy-engine bandwidth between pinned host memory and the device, GB/s:
+    host to device, device to host, and both at once on two streams."""
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    nbytes = X.numel() * X.element_size()
+
+    def timed(fn, nb):
+        fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        t0.record(cur)
+        for _ in range(reps):
+            fn()
+        t1.record(cur)
+        torch.cuda.synchronize()
+        return nb * reps / (t0.elapsed_time(t1) * 1e-3) / 1e9
+
+    def both():
+        cur = torch.cuda.current_stream()
+        sa.wait_stream(cur)
+        sb.wait_stream(cur)
+        with torch.cuda.stream(sa):
+            X.copy_(Xh, non_blocking=True)
+        with torch.cuda.stream(sb):
+            Yh.copy_(Y, non_blocking=True)
+        cur.wait_stream(sa)
+        cur.wait_stream(sb)
+
+    return {"h2d_gbs": timed(lambda: X.copy_(Xh, non_blocking=True), nbytes),
+            "d2h_gbs": timed(lambda: Yh.copy_(Y, non_blocking=True), nbytes),
+            "both_gbs": timed(both, 2 * nbytes)}
 
 
 def _build_case(ax, torch, dev, N, kind, prec, mesh="trilinear", box=None):
@@ -400,6 +434,11 @@ def run(args):
     nbytes = X.numel() * X.element_size()
     e2e = {"value": world * E * n3 / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
+    # the host link's own bound on this leg: the same bytes moved by the copy
+    # engines alone, both directions at once, no kernel
+    link = _host_link(torch, Xh, Yh, X, Y)
+    e2e["link_gbs"] = round(link["both_gbs"], 1)
+    e2e["frac_of_link"] = round((2 * nbytes / e2e_s / 1e9) / link["both_gbs"], 3)
     del Xh, Yh
     op.ax_destroy()
     del X, Y
@@ -407,7 +446,7 @@ def run(args):
 
     detail = {"headline": {"roofline_time_based": {k: roof[k] for k in (
         "t_mem_ms", "t_cmp_ms", "t_meas_ms", "P_eff_gflops", "R_eff_gflops", "frac_time_roofline",
-        "hbm_gbs_achieved")}, "sms": sms, "src_hash": src}}
+        "hbm_gbs_achieved")}, "sms": sms, "src_hash": src}, "host_link": link}
     if not args.no_sweep and rank == 0:
         for name, f in (("sweep", lambda: run_sweep(ax, torch, dev, hbm, clocks.get("sm_mhz"), sms)),
                         ("pcg", lambda: run_pcg(ax, torch, dev)),

@@ -201,14 +201,38 @@ __host__ __device__ constexpr int pick_epb(int F) {
   return best;
 }
 
-// FILL: pick_epb; otherwise the plain 128-thread rule.  Measured on GB300:
-// filling the warps pays for the trilinear kinds in 8-byte arithmetic
-// (double-word, FP64) and for every recompute kind at N1 = 6; the stored
-// and parallelepiped kinds elsewhere, and FP32 at N1 = 10, 12, run faster
-// with the smaller CTAs (more of them per SM).
+// Double-word recompute kernels at N1 = 6 and 10, whose register counts
+// (96-127) let an SM hold only one or two filled CTAs (16-18 warps, stalled
+// at their barriers): elements per CTA and the minimum resident CTAs that
+// bound the registers (0: no override).  Measured on GB300 against the
+// filled shapes, with the register bounds' few spills included: N = 5
+// trilinear 7 elements, 3 CTAs (24.0 -> 32.1 GDOF/s), partial 6, 4
+// (27.1 -> 32.9); N = 9 trilinear 1, 5 (21.9 -> 24.1), partial 3, 2
+// (21.8 -> 26.2).  The stored and parallelepiped kinds (56-96 registers)
+// and N1 = 12 measured no faster in any of the shapes tried.
+__host__ __device__ constexpr int dw_epb(int N1, int KIND) {
+  return N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 7 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 6 : 0)
+         : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 1 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 3 : 0)
+                    : 0;
+}
+__host__ __device__ constexpr int dw_min_ctas(int N1, int KIND) {
+  return N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 3 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 4 : 0)
+         : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 5 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 2 : 0)
+                    : 0;
+}
+
+// Elements per CTA of the per-order kernels (0: the plain 128-thread rule).
+// Measured on GB300: filling the warps (pick_epb) pays for the trilinear
+// kinds in 8-byte arithmetic (double-word, FP64) and for every recompute
+// kind at N1 = 6; the stored and parallelepiped kinds elsewhere, and FP32
+// at N1 = 10, 12, run faster with the smaller CTAs (more of them per SM).
+// The double-word exceptions above come first.
 template <class P, int N1, int KIND>
-constexpr bool kFillWarps =
-    KIND != AX_GEOM_STORED && (N1 == 6 || (sizeof(typename P::S) == 8 && KIND != AX_GEOM_PARALLELEPIPED));
+constexpr int kEpb =
+    (P::kRoll && dw_epb(N1, KIND)) ? dw_epb(N1, KIND)
+    : (KIND != AX_GEOM_STORED && (N1 == 6 || (sizeof(typename P::S) == 8 && KIND != AX_GEOM_PARALLELEPIPED)))
+        ? pick_epb(N1 * N1)
+        : 0;
 
 // Minimum resident CTAs for the register budget (0: no bound): the
 // double-word kernels at N1 = 16 (256-thread CTAs) are held to 128 registers
@@ -216,10 +240,13 @@ constexpr bool kFillWarps =
 // per SM, 5-30% slower); the double-word trilinear kernel at N1 = 12
 // (288-thread CTAs) likewise to two CTAs (96 registers and some spills
 // instead of 119 registers and one CTA: 33% faster; the partial kind
-// measured 5% slower so and keeps its allocation).  Elsewhere no bound is
-// given: even an explicit 1 changes the register allocation for the worse.
+// measured 5% slower so and keeps its allocation); the double-word
+// exceptions of dw_min_ctas.  Elsewhere no bound is given: even an explicit
+// 1 changes the register allocation for the worse.
 template <class P, int N1, int KIND>
-constexpr int kMinCtas = (P::kRoll && (N1 == 16 || (N1 == 12 && KIND == AX_GEOM_TRILINEAR))) ? 2 : 0;
+constexpr int kMinCtas = (P::kRoll && dw_min_ctas(N1, KIND))                                   ? dw_min_ctas(N1, KIND)
+                         : (P::kRoll && (N1 == 16 || (N1 == 12 && KIND == AX_GEOM_TRILINEAR))) ? 2
+                                                                                                 : 0;
 
 // Trilinear kinds: whether an element's first 2 N1 threads compute the axis
 // terms of the geometry (Geometry::axis_terms) for all its threads.  Measured
@@ -231,11 +258,11 @@ template <class P, int N1, int KIND>
 constexpr bool kShareAxis = (KIND == AX_GEOM_TRILINEAR || KIND == AX_GEOM_TRILINEAR_PARTIAL) &&
                             (P::kRoll ? N1 <= 6 : sizeof(typename P::V) == 8);
 
-template <int N1, int EM = 1, bool FILL = false>
+template <int N1, int EM = 1, int EPB0 = 0>
 struct Shape {
   static constexpr int n3 = N1 * N1 * N1;
   static constexpr int F = N1 * N1;  // fibers (threads) per element
-  static constexpr int EPB = EM * (FILL ? pick_epb(F) : (F >= 128 ? 1 : 128 / F));  // elements per CTA (EM: tile variant)
+  static constexpr int EPB = EM * (EPB0 > 0 ? EPB0 : (F >= 128 ? 1 : 128 / F));  // elements per CTA (EM: tile variant)
   static constexpr int threads = F * EPB;
   static constexpr int P = N1 + 1;            // padded row
   static constexpr int ES = N1 * N1 * P;      // padded element size (words)
@@ -531,10 +558,10 @@ struct XGather {
 };
 
 // Shared-memory buffers of one block of EPB elements.
-// FILL: the block shape (kFillWarps for the per-order kernels).
-template <class P, int N1, int KIND, int EM, bool FILL = kFillWarps<P, N1, KIND>>
+// EPB0: the block shape (kEpb for the per-order kernels).
+template <class P, int N1, int KIND, int EM, int EPB0 = kEpb<P, N1, KIND>>
 struct FiberSmem {
-  using Sh = Shape<N1, EM, FILL>;
+  using Sh = Shape<N1, EM, EPB0>;
   using S = typename P::S;
   static constexpr int GW = GeoWords<KIND>::value, GWD = GW > 0 ? GW : 1;
   static constexpr bool AXS = kShareAxis<P, N1, KIND>;
@@ -568,13 +595,13 @@ struct FiberSmem {
 // threads than the order's shape (a CTA shaped for several orders); those
 // threads only take part in the barriers.
 // ---------------------------------------------------------------------------
-template <class P, int N1, int KIND, int EM, bool IDLE, int SCALE, class XS, bool FILL = kFillWarps<P, N1, KIND>>
-__device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, FILL> &sm, const int tid, const int64_t e0,
+template <class P, int N1, int KIND, int EM, bool IDLE, int SCALE, class XS, int EPB0 = kEpb<P, N1, KIND>>
+__device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB0> &sm, const int tid, const int64_t e0,
                                             const int nel, const typename P::S *__restrict__ geo,
                                             const typename P::S *__restrict__ lam, const XS &X,
                                             typename P::IO *__restrict__ Y) {
-  using Sh = Shape<N1, EM, FILL>;
-  using Buf = FiberSmem<P, N1, KIND, EM, FILL>;
+  using Sh = Shape<N1, EM, EPB0>;
+  using Buf = FiberSmem<P, N1, KIND, EM, EPB0>;
   using V = typename P::V;
   using S = typename P::S;
   constexpr int n3 = Sh::n3, EPB = Sh::EPB, ES = Sh::ES;
@@ -841,10 +868,10 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, FIL
 // wide: kScaleIO policies: list of the blocks whose X left the direct range
 // ([0] count, [1] exit counter of the fix-up kernel, [2..] block indices).
 template <class P, int N1, int KIND, int EM>
-__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads, kMinCtas<P, N1, KIND>)
+__global__ void __launch_bounds__(Shape<N1, EM, kEpb<P, N1, KIND>>::threads, kMinCtas<P, N1, KIND>)
     ax_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
                     const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y, int *__restrict__ wide) {
-  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
+  using Sh = Shape<N1, EM, kEpb<P, N1, KIND>>;
   using Buf = FiberSmem<P, N1, KIND, EM>;
   using S = typename P::S;
   constexpr int EPB = Sh::EPB;
@@ -872,10 +899,10 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
 // The fix-up kernel of the kScaleIO policies: the listed blocks again, with X
 // scaled per element; the last CTA to finish clears the list.
 template <class P, int N1, int KIND, int EM>
-__global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::threads)
+__global__ void __launch_bounds__(Shape<N1, EM, kEpb<P, N1, KIND>>::threads)
     ax_fiber_fix_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
                         const typename P::IO *__restrict__ X, typename P::IO *__restrict__ Y, int *__restrict__ wide) {
-  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
+  using Sh = Shape<N1, EM, kEpb<P, N1, KIND>>;
   using Buf = FiberSmem<P, N1, KIND, EM>;
   using S = typename P::S;
   constexpr int EPB = Sh::EPB;
@@ -908,10 +935,10 @@ __global__ void __launch_bounds__(Shape<N1, EM, kFillWarps<P, N1, KIND>>::thread
 
 // Factor export through the same geometry code: G_out [E][7][n3] float64.
 template <class P, int N1, int KIND>
-__global__ void __launch_bounds__(Shape<N1, 1, kFillWarps<P, N1, KIND>>::threads)
+__global__ void __launch_bounds__(Shape<N1, 1, kEpb<P, N1, KIND>>::threads)
     factors_fiber_kernel(int64_t E, const typename P::S *__restrict__ geo, const typename P::S *__restrict__ lam,
                          double *__restrict__ G) {
-  using Sh = Shape<N1, 1, kFillWarps<P, N1, KIND>>;
+  using Sh = Shape<N1, 1, kEpb<P, N1, KIND>>;
   using V = typename P::V;
   using S = typename P::S;
   constexpr int n3 = Sh::n3, EPB = Sh::EPB;
@@ -947,7 +974,7 @@ constexpr int64_t kFixGrid = 256;
 
 template <class P, int N1, int KIND, int EM>
 cudaError_t launch_ax_em(const AxArgs &a) {
-  using Sh = Shape<N1, EM, kFillWarps<P, N1, KIND>>;
+  using Sh = Shape<N1, EM, kEpb<P, N1, KIND>>;
   const int64_t nblk = (a.E + Sh::EPB - 1) / Sh::EPB;
   if (nblk <= 0) return cudaSuccess;
   int64_t grid = a.grid > 0 && a.grid < nblk ? a.grid : nblk;
@@ -1009,7 +1036,7 @@ cudaError_t launch_ax_em(const AxArgs &a) {
 
 template <class P, int N1, int KIND>
 cudaError_t launch_fiber_n(const AxArgs &a, double *G_out) {
-  using Sh = Shape<N1, 1, kFillWarps<P, N1, KIND>>;
+  using Sh = Shape<N1, 1, kEpb<P, N1, KIND>>;
   if (G_out) {
     const int64_t blocks = (a.E + Sh::EPB - 1) / Sh::EPB;
     if (blocks <= 0) return cudaSuccess;

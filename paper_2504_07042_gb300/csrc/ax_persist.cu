@@ -130,7 +130,7 @@ __device__ double cta_sum(double v) {
 template <int N1, int KIND, bool PCG>
 __device__ __noinline__ void ax_tile(unsigned char *smem, const Group &g, int64_t e0, int cnt, const float *X, const float *p,
                         const gidx *gid, float *Y) {
-  using Sh = fiber::Shape<N1, 1, false>;
+  using Sh = fiber::Shape<N1, 1, 0>;
   using Buf = fiber::FiberSmem<P, N1, KIND, 1, false>;
   static_assert(Sh::threads <= kThreads, "order shape wider than the persistent CTA");
   const Buf sm = Buf::carve(smem);
