@@ -201,35 +201,48 @@ __host__ __device__ constexpr int pick_epb(int F) {
   return best;
 }
 
+// Measured exceptions to the shape rules below, per policy (0: double-word,
+// 1: FP32), order and kind: elements per CTA and the minimum resident CTAs
+// that bound the registers (0: no override).
 // Double-word recompute kernels at N1 = 6 and 10, whose register counts
 // (96-127) let an SM hold only one or two filled CTAs (16-18 warps, stalled
-// at their barriers): elements per CTA and the minimum resident CTAs that
-// bound the registers (0: no override).  Measured on GB300 against the
-// filled shapes, with the register bounds' few spills included: N = 5
-// trilinear 7 elements, 3 CTAs (24.0 -> 32.1 GDOF/s), partial 6, 4
-// (27.1 -> 32.9); N = 9 trilinear 1, 5 (21.9 -> 24.1), partial 3, 2
-// (21.8 -> 26.2).  The stored and parallelepiped kinds (56-96 registers)
-// and N1 = 12 measured no faster in any of the shapes tried.
-__host__ __device__ constexpr int dw_epb(int N1, int KIND) {
-  return N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 7 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 6 : 0)
-         : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 1 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 3 : 0)
-                    : 0;
+// at their barriers), measured on GB300 against the filled shapes, with the
+// register bounds' few spills included: N = 5 trilinear 7 elements, 3 CTAs
+// (24.0 -> 32.1 GDOF/s), partial 6, 4 (27.1 -> 32.9); N = 9 trilinear 1, 5
+// (21.9 -> 24.1), partial 3, 2 (21.8 -> 26.2).  Their stored and
+// parallelepiped kinds (56-96 registers) and N1 = 12 measured no faster in
+// any of the shapes tried.
+// FP32 (40-64 registers, mostly faster as they are): N = 5 partial 4
+// elements (153 -> 163), N = 9 parallelepiped 2 (243 -> 251), N = 11 stored
+// 1 element, 4 CTAs (156 -> 172).
+__host__ __device__ constexpr int shape_epb(int pc, int N1, int KIND) {
+  return pc == 0 ? (N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 7 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 6 : 0)
+                    : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 1 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 3 : 0)
+                               : 0)
+                 : (N1 == 6 && KIND == AX_GEOM_TRILINEAR_PARTIAL) ? 4
+                 : (N1 == 10 && KIND == AX_GEOM_PARALLELEPIPED)   ? 2
+                                                                  : 0;
 }
-__host__ __device__ constexpr int dw_min_ctas(int N1, int KIND) {
-  return N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 3 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 4 : 0)
-         : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 5 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 2 : 0)
-                    : 0;
+__host__ __device__ constexpr int shape_min_ctas(int pc, int N1, int KIND) {
+  return pc == 0 ? (N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 3 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 4 : 0)
+                    : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 5 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 2 : 0)
+                               : 0)
+                 : (N1 == 12 && KIND == AX_GEOM_STORED) ? 4
+                                                        : 0;
 }
+// the policy class of shape_epb / shape_min_ctas (-1: none)
+template <class P>
+constexpr int kShapeClass = P::kRoll ? 0 : sizeof(typename P::S) == 4 ? 1 : -1;
 
 // Elements per CTA of the per-order kernels (0: the plain 128-thread rule).
 // Measured on GB300: filling the warps (pick_epb) pays for the trilinear
 // kinds in 8-byte arithmetic (double-word, FP64) and for every recompute
 // kind at N1 = 6; the stored and parallelepiped kinds elsewhere, and FP32
 // at N1 = 10, 12, run faster with the smaller CTAs (more of them per SM).
-// The double-word exceptions above come first.
+// The exceptions of shape_epb come first.
 template <class P, int N1, int KIND>
 constexpr int kEpb =
-    (P::kRoll && dw_epb(N1, KIND)) ? dw_epb(N1, KIND)
+    (kShapeClass<P> >= 0 && shape_epb(kShapeClass<P>, N1, KIND)) ? shape_epb(kShapeClass<P>, N1, KIND)
     : (KIND != AX_GEOM_STORED && (N1 == 6 || (sizeof(typename P::S) == 8 && KIND != AX_GEOM_PARALLELEPIPED)))
         ? pick_epb(N1 * N1)
         : 0;
@@ -240,13 +253,14 @@ constexpr int kEpb =
 // per SM, 5-30% slower); the double-word trilinear kernel at N1 = 12
 // (288-thread CTAs) likewise to two CTAs (96 registers and some spills
 // instead of 119 registers and one CTA: 33% faster; the partial kind
-// measured 5% slower so and keeps its allocation); the double-word
-// exceptions of dw_min_ctas.  Elsewhere no bound is given: even an explicit
-// 1 changes the register allocation for the worse.
+// measured 5% slower so and keeps its allocation); the exceptions of
+// shape_min_ctas.  Elsewhere no bound is given: even an explicit 1 changes
+// the register allocation for the worse.
 template <class P, int N1, int KIND>
-constexpr int kMinCtas = (P::kRoll && dw_min_ctas(N1, KIND))                                   ? dw_min_ctas(N1, KIND)
-                         : (P::kRoll && (N1 == 16 || (N1 == 12 && KIND == AX_GEOM_TRILINEAR))) ? 2
-                                                                                                 : 0;
+constexpr int kMinCtas =
+    (kShapeClass<P> >= 0 && shape_min_ctas(kShapeClass<P>, N1, KIND)) ? shape_min_ctas(kShapeClass<P>, N1, KIND)
+    : (P::kRoll && (N1 == 16 || (N1 == 12 && KIND == AX_GEOM_TRILINEAR)))  ? 2
+                                                                           : 0;
 
 // Trilinear kinds: whether an element's first 2 N1 threads compute the axis
 // terms of the geometry (Geometry::axis_terms) for all its threads.  Measured

@@ -70,10 +70,13 @@ constexpr uint32_t kOffR = 0, kOffS = kOffR + kBytesR, kOffT = kOffS + kBytesS, 
                    kOffGeo = kOffBDT + kBytesB;
 constexpr uint32_t kSmemBytes = kOffGeo + kEPB * kVertexWords * 4 + 64;
 constexpr long long kWaitCycles = 1ll << 32;  // SM clocks (about 2 s) before a wait gives up
-// resident CTAs per SM: the shared memory (about 25 KB each) allows eight;
-// the registers are sized for them (at most 64 per thread) and the tensor
-// memory would allow 512 / 32 = 16
-constexpr int kCtasPerSm = 8;
+// resident CTAs per SM, per kind: the shared memory (about 25 KB each)
+// allows eight, the tensor memory 512 / 32 = 16, and the launch bounds size
+// the registers for them (at most 64 per thread at eight, 73 at seven).
+// Measured on GB300 (GDOF/s at 7 / 8 CTAs): trilinear 208 / 197, stored
+// 193 / 156, parallelepiped 244 / 277, partial 157 / 167.
+template <int KIND>
+constexpr int kCtasPerSm = (KIND == AX_GEOM_TRILINEAR || KIND == AX_GEOM_STORED) ? 7 : 8;
 
 // tcgen05.mma kind::tf32: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2), both
 // K-major, N = 16 (bits 17-22 = N >> 3), M = 128 (bits 24-28 = M >> 4)
@@ -141,7 +144,7 @@ __device__ __forceinline__ float tf32_rn(float v) {
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
     ax_umma_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
                    const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
                    int *__restrict__ err) {
@@ -345,9 +348,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// Launch over a.E elements of order 7: eight CTAs per SM (tensor memory: 64
-// of 512 columns each; 61 registers and 16 KB of shared memory also allow
-// eight), persistent over the tiles of two elements.
+// Launch over a.E elements of order 7: kCtasPerSm CTAs per SM, persistent
+// over the tiles of two elements.
 template <int KIND>
 cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
   const int64_t ntile = (a.E + kEPB - 1) / kEPB;
@@ -360,7 +362,7 @@ cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    grid_cap = kCtasPerSm * sms;
+    grid_cap = kCtasPerSm<KIND> * sms;
   }
   const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
   const int64_t grid = ntile < cap ? ntile : cap;
