@@ -23,7 +23,9 @@
 namespace ax {
 namespace gs {
 
-constexpr int kRedBlocks = 1024;  // stage-1 blocks of every reduction (fixed: determinism)
+// stage-1 blocks of every reduction: fixed, so that every sum has one order
+// (determinism); four per SM of a 152-SM GB300, all resident in one wave
+constexpr int kRedBlocks = 608;
 constexpr int kRedThreads = 256;
 
 template <typename T>
@@ -92,13 +94,44 @@ __global__ void __launch_bounds__(kRedThreads) finish_kernel(const double *__res
 //                      rz_new, rr; test; beta = rz_new / rz  (last block)
 constexpr int kScalars = 16;
 
+// The vector kernels take four nodes per thread and pass (g, g + stride,
+// g + 2 stride, g + 3 stride: each access coalesced across the warp) and
+// issue all their loads before the first store, so that a thread has four
+// independent memory round trips in flight instead of one; the nodes are
+// summed in the same order as one node per pass would.  Two nodes in
+// float64 (the update kernel's five vectors of four doubles spill at the
+// 64 registers that four resident blocks per SM allow).
+template <typename T>
+constexpr int kUnroll = sizeof(T) == 8 ? 2 : 4;
+
 template <typename T>
 __global__ void direction_scatter_kernel(int64_t n_global, const double *__restrict__ S, const T *__restrict__ z,
                                          T *__restrict__ p, const gidx *__restrict__ off,
                                          const gidx *__restrict__ idx, T *__restrict__ U) {
   if (S[6] != 0.0) return;
+  constexpr int kU = kUnroll<T>;
   const T beta = (T)S[11];
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + (kU - 1) * stride < n_global; g += kU * stride) {
+    T zv[kU], pv[kU];
+    gidx b[kU], e[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t q = g + u * stride;
+      zv[u] = z[q];
+      pv[u] = p[q];
+      b[u] = off[q];
+      e[u] = off[q + 1];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const T pg = zv[u] + beta * pv[u];
+      p[g + u * stride] = pg;
+      for (gidx q = b[u]; q < e[u]; ++q) U[idx[q]] = pg;
+    }
+  }
+  for (; g < n_global; g += stride) {
     const T pg = z[g] + beta * p[g];
     p[g] = pg;
     for (gidx q = off[g]; q < off[g + 1]; ++q) U[idx[q]] = pg;
@@ -106,21 +139,48 @@ __global__ void direction_scatter_kernel(int64_t n_global, const double *__restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152)
     gather_dot_alpha_kernel(int64_t n_global, const gidx *__restrict__ off, const gidx *__restrict__ idx,
                             const T *__restrict__ Y, T *__restrict__ w, const uint8_t *__restrict__ mask,
                             const T *__restrict__ p, double *__restrict__ partial, unsigned *__restrict__ cnt,
                             double *__restrict__ S) {
   if (S[6] != 0.0) return;
+  constexpr int kU = kUnroll<T>;
   T d = T(0);
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_global; g += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + (kU - 1) * stride < n_global; g += kU * stride) {
+    T s[kU], pv[kU];
+    gidx b[kU], e[kU];
+    bool mv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t q = g + u * stride;
+      b[u] = off[q];
+      e[u] = off[q + 1];
+      pv[u] = p[q];
+      mv[u] = mask && mask[q];
+    }
+    // the first local copy of the four nodes at once (a node without any
+    // copy sums to zero), then the rest
+#pragma unroll
+    for (int u = 0; u < kU; ++u) s[u] = b[u] < e[u] ? T(0) + Y[idx[b[u]]] : T(0);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      for (gidx q = b[u] + 1; q < e[u]; ++q) s[u] += Y[idx[q]];
+      if (mv[u]) s[u] = T(0);
+      w[g + u * stride] = s[u];
+      d += pv[u] * s[u];
+    }
+  }
+  for (; g < n_global; g += stride) {
     T s = T(0);
     for (gidx q = off[g]; q < off[g + 1]; ++q) s += Y[idx[q]];
     if (mask && mask[g]) s = T(0);
     w[g] = s;
     d += p[g] * s;
   }
-  red::block_reduce_store((double)d, partial + blockIdx.x);
+  red::block_reduce2_store<T>(d, T(0), partial + blockIdx.x, nullptr);
   if (!red::arrive_last(cnt)) return;
   const double pw = red::sum_partials(partial, gridDim.x);
   if (threadIdx.x == 0) {
@@ -130,15 +190,44 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, kRedBlocks / 152)
     update_check_kernel(int64_t n, double *__restrict__ S, const T *__restrict__ p, const T *__restrict__ w,
                         T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, const T *__restrict__ inv_diag,
                         const uint8_t *__restrict__ mask, double *__restrict__ part_rz, double *__restrict__ part_rr,
                         unsigned *__restrict__ cnt) {
   if (S[6] != 0.0) return;
+  constexpr int kU = kUnroll<T>;
   const T alpha = (T)S[10];
   T rz = T(0), rr = T(0);
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + (kU - 1) * stride < n; g += kU * stride) {
+    T xv[kU], pv[kU], rv[kU], wv[kU], iv[kU];
+    bool mv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t q = g + u * stride;
+      xv[u] = x[q];
+      pv[u] = p[q];
+      rv[u] = r[q];
+      wv[u] = w[q];
+      iv[u] = inv_diag ? inv_diag[q] : T(1);
+      mv[u] = mask && mask[q];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int64_t q = g + u * stride;
+      const T rg = rv[u] - alpha * wv[u];
+      T zg = inv_diag ? rg * iv[u] : rg;
+      if (mv[u]) zg = T(0);
+      x[q] = xv[u] + alpha * pv[u];
+      r[q] = rg;
+      z[q] = zg;
+      rz += rg * zg;
+      rr += rg * rg;
+    }
+  }
+  for (; g < n; g += stride) {
     const T xg = x[g] + alpha * p[g];
     const T rg = r[g] - alpha * w[g];
     T zg = inv_diag ? rg * inv_diag[g] : rg;
@@ -149,12 +238,10 @@ __global__ void __launch_bounds__(kRedThreads)
     rz += rg * zg;
     rr += rg * rg;
   }
-  red::block_reduce_store((double)rz, part_rz + blockIdx.x);
-  __syncthreads();
-  red::block_reduce_store((double)rr, part_rr + blockIdx.x);
+  red::block_reduce2_store<T>(rz, rr, part_rz + blockIdx.x, part_rr + blockIdx.x);
   if (!red::arrive_last(cnt)) return;
-  const double rz_new = red::sum_partials(part_rz, gridDim.x);
-  const double rr_new = red::sum_partials(part_rr, gridDim.x);
+  double rz_new, rr_new;
+  red::sum_partials2(part_rz, part_rr, gridDim.x, rz_new, rr_new);
   if (threadIdx.x == 0) {
     S[4] = rz_new;
     S[2] = rr_new;
