@@ -52,7 +52,7 @@ TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.570368e6 + 90.04
 
 
 # the sources that define the headline kernel (double-word AxLocal, N = 7)
-KERNEL_SOURCES = ("ax_fiber.cuh", "dw.cuh", "inst_fiber.inc", "ax_dw_g1.cu", "tables.cuh", "ax_internal.h",
+KERNEL_SOURCES = ("ax_fiber.cuh", "dw.cuh", "dw2.cuh", "inst_fiber.inc", "ax_dw_g1.cu", "tables.cuh", "ax_internal.h",
                   "gll.cpp", "gll.h")
 
 

@@ -28,6 +28,7 @@
 
 #include "ax_internal.h"
 #include "dw.cuh"
+#include "dw2.cuh"
 #include "tables.cuh"
 
 namespace ax {
@@ -186,6 +187,21 @@ __device__ __forceinline__ void contract(const typename P::C *__restrict__ eo, c
   }
 }
 
+// The double-word fiber product at even orders runs its two dot products per
+// output pair in the lanes of packed FP32x2 instructions (dw2.cuh; the same
+// roundings in the same order: bit-identical results, about half the issue
+// slots for the products); eo2: the order's paired table.
+template <class P, int N1>
+constexpr bool kPairedDW = P::kRoll && (N1 % 2) == 0;
+template <class P, int N1>
+__device__ __forceinline__ void contract_p(const typename P::C *__restrict__ eo, const float4 *__restrict__ eo2,
+                                           const typename P::V *in, typename P::V *out) {
+  if constexpr (kPairedDW<P, N1>)
+    dw2::contract<N1>(eo2, in, out);
+  else
+    contract<P, N1>(eo, in, out);
+}
+
 // Elements per CTA for F threads per element: at least 128 threads, and
 // among up to about four times that many elements (at most 512 threads) the
 // count that leaves the fewest idle lanes in the last warp (N1 = 6: 7
@@ -211,7 +227,9 @@ __host__ __device__ constexpr int pick_epb(int F) {
 // (24.0 -> 32.1 GDOF/s), partial 6, 4 (27.1 -> 32.9); N = 9 trilinear 1, 5
 // (21.9 -> 24.1), partial 3, 2 (21.8 -> 26.2).  Their stored and
 // parallelepiped kinds (56-96 registers) and N1 = 12 measured no faster in
-// any of the shapes tried.
+// any of the shapes tried.  With the packed fiber product (dw2.cuh) the
+// trilinear kernel at N1 = 8 takes 127 registers unbounded (four CTAs per
+// SM); bounded to five CTAs (96 registers, no spills) it runs 2.4% faster.
 // FP32 (40-64 registers, mostly faster as they are): N = 5 partial 4
 // elements (153 -> 163), N = 9 parallelepiped 2 (243 -> 251), N = 11 stored
 // 1 element, 4 CTAs (156 -> 172).
@@ -224,7 +242,8 @@ __host__ __device__ constexpr int shape_epb(int pc, int N1, int KIND) {
                                                                   : 0;
 }
 __host__ __device__ constexpr int shape_min_ctas(int pc, int N1, int KIND) {
-  return pc == 0 ? (N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 3 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 4 : 0)
+  return pc == 0 ? (N1 == 8    ? (KIND == AX_GEOM_TRILINEAR ? 5 : 0)
+                    : N1 == 6  ? (KIND == AX_GEOM_TRILINEAR ? 3 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 4 : 0)
                     : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 5 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 2 : 0)
                                : 0)
                  : (N1 == 12 && KIND == AX_GEOM_STORED) ? 4
@@ -633,6 +652,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
   const int qa = q % N1, qb = q / N1;
   const typename P::C *eoD = c_eoD + tab_off_D(N1);
   const typename P::C *eoDT = c_eoDT + tab_off_D(N1);
+  const float4 *eo2D = c_eo2D + tab_off_P(N1), *eo2DT = c_eo2DT + tab_off_P(N1);
   const typename P::C *cw = c_w + tab_off_v(N1);
   const typename P::C *cx = c_x + tab_off_v(N1);
   const S *const sgeo_z = sm.sgeo + (act ? z : 0) * Buf::GWD;
@@ -733,7 +753,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
     V fin_[N1], fout[N1];
 #pragma unroll
     for (int n = 0; n < N1; ++n) fin_[n] = P::ld(x_e + base + n * stride);
-    contract<P, N1>(eoD, fin_, fout);
+    contract_p<P, N1>(eoD, eo2D, fin_, fout);
 #pragma unroll
     for (int n = 0; n < N1; ++n) dst[base + n * stride] = P::st(fout[n]);
   };
@@ -779,7 +799,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
       V fin_[N1], fout[N1];
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(buf + base + n * stride);
-      contract<P, N1>(eoDT, fin_, fout);
+      contract_p<P, N1>(eoDT, eo2DT, fin_, fout);
       if (kYtRegs && ph == 3) {
 #pragma unroll
         for (int n = 0; n < N1; ++n) yt[kYtRegs ? n : 0] = fout[n];
@@ -821,7 +841,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
       V fin_[N1];
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(x_e + ft + n * str_t);
-      contract<P, N1>(eoD, fin_, tf);
+      contract_p<P, N1>(eoD, eo2D, fin_, tf);
     }
     __syncthreads();  // every r/s fiber product is in B0, B1
     V yt[N1];
@@ -845,7 +865,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
         s_e[sidx] = P::st(o3[1]);
         tf[k] = o3[2];
       }
-      contract<P, N1>(eoDT, tf, yt);
+      contract_p<P, N1>(eoDT, eo2DT, tf, yt);
     }
     __syncthreads();  // every r, s value is in B0, B1
 #pragma unroll
@@ -856,7 +876,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
       V fin_[N1], fout[N1];
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(buf + base + n * stride);
-      contract<P, N1>(eoDT, fin_, fout);
+      contract_p<P, N1>(eoDT, eo2DT, fin_, fout);
 #pragma unroll
       for (int n = 0; n < N1; ++n) buf[base + n * stride] = P::st(fout[n]);
     }

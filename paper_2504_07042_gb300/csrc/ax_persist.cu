@@ -131,7 +131,7 @@ template <int N1, int KIND, bool PCG>
 __device__ __noinline__ void ax_tile(unsigned char *smem, const Group &g, int64_t e0, int cnt, const float *X, const float *p,
                         const gidx *gid, float *Y) {
   using Sh = fiber::Shape<N1, 1, 0>;
-  using Buf = fiber::FiberSmem<P, N1, KIND, 1, false>;
+  using Buf = fiber::FiberSmem<P, N1, KIND, 1, 0>;
   static_assert(Sh::threads <= kThreads, "order shape wider than the persistent CTA");
   const Buf sm = Buf::carve(smem);
   const int tid = threadIdx.x;
@@ -139,10 +139,10 @@ __device__ __noinline__ void ax_tile(unsigned char *smem, const Group &g, int64_
   for (int64_t b = e0; b < e0 + cnt; b += Sh::EPB) {
     const int nel = (int)((e0 + cnt - b) < Sh::EPB ? (e0 + cnt - b) : Sh::EPB);
     if constexpr (PCG) {
-      fiber::fiber_block<P, N1, KIND, 1, true, 0, fiber::XGather<float>, false>(
+      fiber::fiber_block<P, N1, KIND, 1, true, 0, fiber::XGather<float>, 0>(
           sm, tid, b, nel, (const float *)g.geo, (const float *)g.lam, fiber::XGather<float>{p, gid + g.loc}, Yg);
     } else {
-      fiber::fiber_block<P, N1, KIND, 1, true, 0, fiber::XDirect<float>, false>(
+      fiber::fiber_block<P, N1, KIND, 1, true, 0, fiber::XDirect<float>, 0>(
           sm, tid, b, nel, (const float *)g.geo, (const float *)g.lam, fiber::XDirect<float>{X + g.loc}, Yg);
     }
   }
@@ -341,7 +341,7 @@ namespace {
 
 template <int N1, int KIND>
 constexpr size_t smem_of() {
-  return fiber::FiberSmem<P, N1, KIND, 1, false>::bytes;
+  return fiber::FiberSmem<P, N1, KIND, 1, 0>::bytes;
 }
 template <int KIND>
 size_t smem_max() {
