@@ -193,11 +193,23 @@ __device__ __forceinline__ void contract(const typename P::C *__restrict__ eo, c
 // slots for the products); eo2: the order's paired table.
 template <class P, int N1>
 constexpr bool kPairedDW = P::kRoll && (N1 % 2) == 0;
-template <class P, int N1>
+// FP32 likewise (the same products per lane, bit-identical).  Measured on
+// GB300 against the scalar product: N = 7 trilinear 238 -> 255 GDOF/s,
+// parallelepiped 314 -> 324, stored 180 -> 188, N = 3, 9 trilinear +5%,
+// N = 15 trilinear 172 -> 178 (with the two-CTA register bound of
+// shape_min_ctas; unbounded the kernel takes 161 registers and one CTA per
+// SM: 131); the partial kind at N1 = 8 measured 6% slower and keeps the
+// scalar product.
+template <class P, int N1, int KIND>
+constexpr bool kPairedF32 = !P::kRoll && sizeof(typename P::V) == 4 && (N1 % 2) == 0 &&
+                            !(N1 == 8 && KIND == AX_GEOM_TRILINEAR_PARTIAL);
+template <class P, int N1, int KIND>
 __device__ __forceinline__ void contract_p(const typename P::C *__restrict__ eo, const float4 *__restrict__ eo2,
                                            const typename P::V *in, typename P::V *out) {
   if constexpr (kPairedDW<P, N1>)
     dw2::contract<N1>(eo2, in, out);
+  else if constexpr (kPairedF32<P, N1, KIND>)
+    dw2::contract_f32<N1>(eo2, in, out);
   else
     contract<P, N1>(eo, in, out);
 }
@@ -232,7 +244,8 @@ __host__ __device__ constexpr int pick_epb(int F) {
 // SM); bounded to five CTAs (96 registers, no spills) it runs 2.4% faster.
 // FP32 (40-64 registers, mostly faster as they are): N = 5 partial 4
 // elements (153 -> 163), N = 9 parallelepiped 2 (243 -> 251), N = 11 stored
-// 1 element, 4 CTAs (156 -> 172).
+// 1 element, 4 CTAs (156 -> 172); N1 = 16 two CTAs (the packed fiber
+// product, kPairedF32, would otherwise take 161 registers).
 __host__ __device__ constexpr int shape_epb(int pc, int N1, int KIND) {
   return pc == 0 ? (N1 == 6    ? (KIND == AX_GEOM_TRILINEAR ? 7 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 6 : 0)
                     : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 1 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 3 : 0)
@@ -247,6 +260,7 @@ __host__ __device__ constexpr int shape_min_ctas(int pc, int N1, int KIND) {
                     : N1 == 10 ? (KIND == AX_GEOM_TRILINEAR ? 5 : KIND == AX_GEOM_TRILINEAR_PARTIAL ? 2 : 0)
                                : 0)
                  : (N1 == 12 && KIND == AX_GEOM_STORED) ? 4
+                 : N1 == 16                              ? 2
                                                         : 0;
 }
 // the policy class of shape_epb / shape_min_ctas (-1: none)
@@ -753,7 +767,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
     V fin_[N1], fout[N1];
 #pragma unroll
     for (int n = 0; n < N1; ++n) fin_[n] = P::ld(x_e + base + n * stride);
-    contract_p<P, N1>(eoD, eo2D, fin_, fout);
+    contract_p<P, N1, KIND>(eoD, eo2D, fin_, fout);
 #pragma unroll
     for (int n = 0; n < N1; ++n) dst[base + n * stride] = P::st(fout[n]);
   };
@@ -799,7 +813,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
       V fin_[N1], fout[N1];
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(buf + base + n * stride);
-      contract_p<P, N1>(eoDT, eo2DT, fin_, fout);
+      contract_p<P, N1, KIND>(eoDT, eo2DT, fin_, fout);
       if (kYtRegs && ph == 3) {
 #pragma unroll
         for (int n = 0; n < N1; ++n) yt[kYtRegs ? n : 0] = fout[n];
@@ -841,7 +855,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
       V fin_[N1];
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(x_e + ft + n * str_t);
-      contract_p<P, N1>(eoD, eo2D, fin_, tf);
+      contract_p<P, N1, KIND>(eoD, eo2D, fin_, tf);
     }
     __syncthreads();  // every r/s fiber product is in B0, B1
     V yt[N1];
@@ -865,7 +879,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
         s_e[sidx] = P::st(o3[1]);
         tf[k] = o3[2];
       }
-      contract_p<P, N1>(eoDT, eo2DT, tf, yt);
+      contract_p<P, N1, KIND>(eoDT, eo2DT, tf, yt);
     }
     __syncthreads();  // every r, s value is in B0, B1
 #pragma unroll
@@ -876,7 +890,7 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
       V fin_[N1], fout[N1];
 #pragma unroll
       for (int n = 0; n < N1; ++n) fin_[n] = P::ld(buf + base + n * stride);
-      contract_p<P, N1>(eoDT, eo2DT, fin_, fout);
+      contract_p<P, N1, KIND>(eoDT, eo2DT, fin_, fout);
 #pragma unroll
       for (int n = 0; n < N1; ++n) buf[base + n * stride] = P::st(fout[n]);
     }

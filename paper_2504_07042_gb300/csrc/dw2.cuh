@@ -129,5 +129,31 @@ __device__ __forceinline__ void contract(const float4 *__restrict__ eo2, const d
   }
 }
 
+// Even-odd fiber product of even order N1 in FP32 with the P and Q dot
+// products of each output pair in the two lanes (the float policy's
+// contract: the same products and fused multiply-adds per lane, in the same
+// order).  The constants come from the same paired table, whose high words
+// are the float constants of the scalar table.
+template <int N1>
+__device__ __forceinline__ void contract_f32(const float4 *__restrict__ eo2, const float *in, float *out) {
+  static_assert((N1 & 1) == 0, "packed fiber product: even orders only");
+  constexpr int c = N1 / 2;
+  f2 y[c];
+#pragma unroll
+  for (int m = 0; m < c; ++m) y[m] = make_float2(in[m] + in[N1 - 1 - m], in[m] - in[N1 - 1 - m]);
+#pragma unroll
+  for (int i = 0; i < c; ++i) {
+    float4 k = eo2[i * c];
+    f2 pq = mul(make_float2(k.x, k.y), y[0]);
+#pragma unroll
+    for (int m = 1; m < c; ++m) {
+      k = eo2[i * c + m];
+      pq = fma(make_float2(k.x, k.y), y[m], pq);
+    }
+    out[i] = pq.x + pq.y;
+    out[N1 - 1 - i] = pq.y - pq.x;
+  }
+}
+
 }  // namespace dw2
 }  // namespace ax
