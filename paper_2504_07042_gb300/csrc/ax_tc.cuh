@@ -295,14 +295,15 @@ cudaError_t launch_tc_kind(const AxArgs &a, const float *Dp) {
 
 template <int MODE, int N1>
 cudaError_t launch_tc_n(const AxArgs &a, const float *Dp) {
-  if constexpr (MODE == kTF32 && N1 == 8) {
-    // order 7 in TF32: tcgen05 (tile variant 1 selects the mma.sync kernel below)
+  if constexpr (N1 == 8) {
+    // order 7: tcgen05 in every format (operand format = MODE; tile variant 1
+    // selects the mma.sync kernel below)
     if (a.tile != 1) {
       switch (a.kind) {
-        case AX_GEOM_STORED: return umma::launch_kind<AX_GEOM_STORED>(a, Dp);
-        case AX_GEOM_TRILINEAR: return umma::launch_kind<AX_GEOM_TRILINEAR>(a, Dp);
-        case AX_GEOM_PARALLELEPIPED: return umma::launch_kind<AX_GEOM_PARALLELEPIPED>(a, Dp);
-        case AX_GEOM_TRILINEAR_PARTIAL: return umma::launch_kind<AX_GEOM_TRILINEAR_PARTIAL>(a, Dp);
+        case AX_GEOM_STORED: return umma::launch_kind<AX_GEOM_STORED, MODE>(a, Dp);
+        case AX_GEOM_TRILINEAR: return umma::launch_kind<AX_GEOM_TRILINEAR, MODE>(a, Dp);
+        case AX_GEOM_PARALLELEPIPED: return umma::launch_kind<AX_GEOM_PARALLELEPIPED, MODE>(a, Dp);
+        case AX_GEOM_TRILINEAR_PARTIAL: return umma::launch_kind<AX_GEOM_TRILINEAR_PARTIAL, MODE>(a, Dp);
         default: return cudaErrorInvalidValue;
       }
     }

@@ -39,17 +39,59 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ax_fiber.cuh"
 
 namespace ax {
 namespace umma {
 
 constexpr int kN1 = 8, kN3 = 512, kEPB = 2, kThreads = 128, kTmemCols = 32;
-// operand buffers: r (rows (j,k,e), K = i), s (rows (i,k,e), K = j), t (rows (i,j,e), K = k);
-// strides from a search over the threads' store patterns: r free of bank
-// conflicts, s and t at most 2-way (a dense r, also 2-way, measured 3% slower)
-constexpr uint32_t kLboR = 448, kSboR = 288, kLboS = 128, kSboS = 272, kLboT = 128, kSboT = 272;
-constexpr uint32_t kBytesR = 4896, kBytesS = 4336, kBytesT = 4336;
+
+// Operand formats: OP 0 = TF32 (tcgen05.mma kind::tf32, 4-byte operands,
+// K = 8 per instruction: the 8 values of a row fill it), OP 1 = BF16 and
+// OP 2 = FP16 (kind::f16, 2-byte operands, K = 16 per instruction: a row's 8
+// values fill the first K half; the second K half of each A operand is the
+// first one again (LBO = 0) and that of each B operand is zero, so it adds
+// nothing).  Per format: the operand buffers r (rows (j,k,e), K = i),
+// s (rows (i,k,e), K = j), t (rows (i,j,e), K = k) with their LBO and SBO,
+// the B buffers of D and D^T, and the instruction descriptor: D float32
+// (bits 4-5 = 1), A and B types (bits 7-9, 10-12: TF32 = 2 in kind::tf32;
+// F16 = 0, BF16 = 1 in kind::f16), both K-major, N = 16 (bits 17-22 =
+// N >> 3), M = 128 (bits 24-28 = M >> 4).
+template <int OP>
+struct Fmt;
+template <>
+struct Fmt<0> {
+  static constexpr int kEsz = 4;  // bytes per operand value
+  // strides from a search over the threads' store patterns: r free of bank
+  // conflicts, s and t at most 2-way (a dense r, also 2-way, measured 3% slower)
+  static constexpr uint32_t kLboR = 448, kSboR = 288, kLboS = 128, kSboS = 272, kLboT = 128, kSboT = 272;
+  static constexpr uint32_t kBytesR = 4896, kBytesS = 4336, kBytesT = 4336;
+  // B buffers: 24 rows x K 8 (two K cores of 4 values)
+  static constexpr uint32_t kLboB = 128, kSboB = 256, kBytesB = 768;
+  static constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+};
+template <int OP>
+struct Fmt16 {
+  static constexpr int kEsz = 2;
+  // one K core per row group: r dense (its 8-byte staging stores cover
+  // whole rows), s with SBO = 160 bytes (staging and r/s stores free of bank
+  // conflicts), t with SBO = 144 (2-way staging stores, conflict-free 16-byte
+  // row stores)
+  static constexpr uint32_t kLboR = 0, kSboR = 128, kLboS = 0, kSboS = 160, kLboT = 0, kSboT = 144;
+  static constexpr uint32_t kBytesR = 16 * 128, kBytesS = 16 * 160, kBytesT = 16 * 144;
+  // B buffers: 24 rows x the first K half (three row groups of 128 bytes),
+  // then the zero second K half at LBO = 384
+  static constexpr uint32_t kLboB = 384, kSboB = 128, kBytesB = 768;
+  static constexpr uint32_t kIdesc =
+      (1u << 4) | ((OP == 1 ? 1u : 0u) << 7) | ((OP == 1 ? 1u : 0u) << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+};
+template <>
+struct Fmt<1> : Fmt16<1> {};
+template <>
+struct Fmt<2> : Fmt16<2> {};
 // exchange buffers (x0, x1, then Y_r, Y_s): [e][k][j][i] float32 with pitches
 // 576, 72, 8, 1 floats (the k pitch 72 = 8 mod 32 keeps the stride-8 row
 // writes and the t-fiber reads free of bank conflicts); apart from the
@@ -62,13 +104,16 @@ constexpr uint32_t kBytesX = 2 * kXe * 4;
 // 0-7 of its 16-column accumulator, the window starting at row 0 in columns
 // 8-15.  So the r and s products share one accumulator (x0 | x1, then
 // Y_r | Y_s) and t has the next: 32 TMEM columns per CTA
-constexpr uint32_t kLboB = 128, kSboB = 256, kBytesB = 768;
 // shared memory: r, s, t operand buffers, the two exchange buffers, the D
 // and D^T B buffers, geometry records, mbarrier, TMEM address
-constexpr uint32_t kOffR = 0, kOffS = kOffR + kBytesR, kOffT = kOffS + kBytesS, kOffX0 = kOffT + kBytesT,
-                   kOffX1 = kOffX0 + kBytesX, kOffBD = kOffX1 + kBytesX, kOffBDT = kOffBD + kBytesB,
-                   kOffGeo = kOffBDT + kBytesB;
-constexpr uint32_t kSmemBytes = kOffGeo + kEPB * kVertexWords * 4 + 64;
+template <int OP>
+struct Smem {
+  using F = Fmt<OP>;
+  static constexpr uint32_t kOffR = 0, kOffS = kOffR + F::kBytesR, kOffT = kOffS + F::kBytesS,
+                            kOffX0 = kOffT + F::kBytesT, kOffX1 = kOffX0 + kBytesX, kOffBD = kOffX1 + kBytesX,
+                            kOffBDT = kOffBD + F::kBytesB, kOffGeo = kOffBDT + F::kBytesB;
+  static constexpr uint32_t kBytes = kOffGeo + kEPB * kVertexWords * 4 + 64;
+};
 constexpr long long kWaitCycles = 1ll << 32;  // SM clocks (about 2 s) before a wait gives up
 // resident CTAs per SM, per kind: the shared memory (about 25 KB each)
 // allows eight, the tensor memory 512 / 32 = 16, and the launch bounds size
@@ -78,13 +123,13 @@ constexpr long long kWaitCycles = 1ll << 32;  // SM clocks (about 2 s) before a 
 template <int KIND>
 constexpr int kCtasPerSm = (KIND == AX_GEOM_TRILINEAR || KIND == AX_GEOM_STORED) ? 7 : 8;
 
-// tcgen05.mma kind::tf32: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2), both
-// K-major, N = 16 (bits 17-22 = N >> 3), M = 128 (bits 24-28 = M >> 4)
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-
-// byte offset of (row, k) in a K-major no-swizzle core-matrix layout
+// byte offset of (row, k) in a K-major no-swizzle core-matrix layout of
+// ESZ-byte values (16 bytes of K per core-matrix row)
+template <int ESZ = 4>
 __host__ __device__ constexpr uint32_t cm_off(int row, int k, uint32_t lbo, uint32_t sbo) {
-  return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 2) * lbo + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 3) * 4u;
+  constexpr int per = 16 / ESZ;  // values per core-matrix row
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / per) * lbo + (uint32_t)(row & 7) * 16u +
+         (uint32_t)(k % per) * ESZ;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -93,11 +138,18 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo, uint32_t 
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate));
+template <int OP>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+  if constexpr (OP == 0)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(Fmt<OP>::kIdesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(Fmt<OP>::kIdesc), "r"(accumulate));
 }
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
@@ -142,31 +194,67 @@ __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float(r);
 }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// a value in the operand format (rounded to nearest): the TF32 bits, or the
+// 16-bit code in the low half
+template <int OP>
+__device__ __forceinline__ uint32_t code(float v) {
+  if constexpr (OP == 0)
+    return __float_as_uint(tf32_rn(v));
+  else if constexpr (OP == 1)
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+  else
+    return (uint32_t)__half_as_ushort(__float2half_rn(v));
+}
+// one coded value stored at base + off
+template <int OP>
+__device__ __forceinline__ void st_code(unsigned char *base, uint32_t off, uint32_t c) {
+  if constexpr (OP == 0)
+    *(uint32_t *)(base + off) = c;
+  else
+    *(uint16_t *)(base + off) = (uint16_t)c;
+}
+// four coded consecutive K values of one row (16-byte aligned for TF32, 8-byte for 16-bit)
+template <int OP>
+__device__ __forceinline__ void st_code4(unsigned char *base, uint32_t off, const uint32_t c[4]) {
+  if constexpr (OP == 0)
+    *(uint4 *)(base + off) = make_uint4(c[0], c[1], c[2], c[3]);
+  else
+    *(uint2 *)(base + off) = make_uint2(c[0] | (c[1] << 16), c[2] | (c[3] << 16));
+}
+template <int OP>
+__device__ __forceinline__ void st_op(unsigned char *base, uint32_t off, float v) {
+  st_code<OP>(base, off, code<OP>(v));
+}
 
-template <int KIND>
+template <int KIND, int OP>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
     ax_umma_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
                    const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
                    int *__restrict__ err) {
   using P = fiber::Native<float>;
+  using F = Fmt<OP>;
+  using L = Smem<OP>;
+  constexpr int ESZ = F::kEsz;
   constexpr int GW = fiber::GeoWords<KIND>::value;
   extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char *bufR = sm + kOffR, *bufS = sm + kOffS, *bufT = sm + kOffT;
-  float *sgeo = (float *)(sm + kOffGeo);
-  uint64_t *bar = (uint64_t *)(sm + kOffGeo + kEPB * kVertexWords * 4);
+  unsigned char *bufR = sm + L::kOffR, *bufS = sm + L::kOffS, *bufT = sm + L::kOffT;
+  float *sgeo = (float *)(sm + L::kOffGeo);
+  uint64_t *bar = (uint64_t *)(sm + L::kOffGeo + kEPB * kVertexWords * 4);
   uint32_t *tslot = (uint32_t *)(bar + 1);
   __shared__ int abort_cta;
   const int tid = threadIdx.x, warp = tid >> 5;
   const float *cw = fiber::c_w + tab_off_v(kN1);
   const float *cx = fiber::c_x + tab_off_v(kN1);
 
-  // D (rows a, K = m) and D^T (rows m, K = a), TF32, at rows 8..15 of their
-  // 24-row buffers, zero elsewhere
-  for (int q = tid; q < 2 * 24 * 8; q += kThreads) {
-    const int which = q / 192, row = (q % 192) >> 3, k = q & 7, a = row - 8;
+  // D (rows a, K = m) and D^T (rows m, K = a), in the operand format, at
+  // rows 8..15 of their 24-row buffers, zero elsewhere (and in the second K
+  // half of the 16-bit formats)
+  constexpr int kKB = OP == 0 ? 8 : 16;  // K values per B row
+  for (int q = tid; q < 2 * 24 * kKB; q += kThreads) {
+    const int which = q / (24 * kKB), row = (q % (24 * kKB)) / kKB, k = q % kKB, a = row - 8;
     float v = 0.0f;
-    if (a >= 0 && a < kN1) v = tf32_rn(which == 0 ? Dp[a * kN1 + k] : Dp[k * kN1 + a]);
-    *(float *)(sm + (which == 0 ? kOffBD : kOffBDT) + cm_off(row, k, kLboB, kSboB)) = v;
+    if (a >= 0 && a < kN1 && k < kN1) v = which == 0 ? Dp[a * kN1 + k] : Dp[k * kN1 + a];
+    st_op<OP>(sm + (which == 0 ? L::kOffBD : L::kOffBDT), cm_off<ESZ>(row, k, F::kLboB, F::kSboB), v);
   }
   if (tid == 0) {
     abort_cta = 0;
@@ -185,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
   const uint32_t tmem = *tslot;
   const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
   const uint32_t aR = smem_u32(bufR), aS = smem_u32(bufS), aT = smem_u32(bufT);
-  const uint32_t aBD = smem_u32(sm + kOffBD), aBDT = smem_u32(sm + kOffBDT);
+  const uint32_t aBD = smem_u32(sm + L::kOffBD), aBDT = smem_u32(sm + L::kOffBDT);
   // this thread as a row of each direction: L = a + 8 b + 64 e
   const int la = tid & 7, lb = (tid >> 3) & 7, le = tid >> 6;
   uint32_t phase = 0;
@@ -222,14 +310,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
     for (int s = 0; s < 2; ++s) {
       const int f = tid + kThreads * s;
       const int i0 = 4 * (f & 1), j = (f >> 1) & 7, k = (f >> 4) & 7, e = f >> 7;
-      float4 v = xnext[s];
-      v = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));  // round, not truncate
-      *(float4 *)(bufR + cm_off(j + 8 * k + 64 * e, i0, kLboR, kSboR)) = v;
-      const float c[4] = {v.x, v.y, v.z, v.w};
+      const float4 v = xnext[s];
+      // rounded to the format once (to nearest, not truncated)
+      const uint32_t c[4] = {code<OP>(v.x), code<OP>(v.y), code<OP>(v.z), code<OP>(v.w)};
+      st_code4<OP>(bufR, cm_off<ESZ>(j + 8 * k + 64 * e, i0, F::kLboR, F::kSboR), c);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        *(float *)(bufS + cm_off(i0 + q + 8 * k + 64 * e, j, kLboS, kSboS)) = c[q];
-        *(float *)(bufT + cm_off(i0 + q + 8 * j + 64 * e, k, kLboT, kSboT)) = c[q];
+        st_code<OP>(bufS, cm_off<ESZ>(i0 + q + 8 * k + 64 * e, j, F::kLboS, F::kSboS), c[q]);
+        st_code<OP>(bufT, cm_off<ESZ>(i0 + q + 8 * j + 64 * e, k, F::kLboT, F::kSboT), c[q]);
       }
     }
     if constexpr (GW > 0) {
@@ -241,9 +329,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
     // 2. forward MMAs
     if (tid == 0 && !abort_cta) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      mma_tf32(tmem, desc(aR, kLboR, kSboR), desc(aBD + kSboB, kLboB, kSboB), 0u);
-      mma_tf32(tmem, desc(aS, kLboS, kSboS), desc(aBD, kLboB, kSboB), 1u);
-      mma_tf32(tmem + 16, desc(aT, kLboT, kSboT), desc(aBD + kSboB, kLboB, kSboB), 0u);
+      mma<OP>(tmem, desc(aR, F::kLboR, F::kSboR), desc(aBD + F::kSboB, F::kLboB, F::kSboB), 0u);
+      mma<OP>(tmem, desc(aS, F::kLboS, F::kSboS), desc(aBD, F::kLboB, F::kSboB), 1u);
+      mma<OP>(tmem + 16, desc(aT, F::kLboT, F::kSboT), desc(aBD + F::kSboB, F::kLboB, F::kSboB), 0u);
       commit(smem_u32(bar));
     }
     // thread 0 waits for the MMAs (bounded); the others sleep in the barrier
@@ -261,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
     tmem_ld8(tlane + 16, x2);
     tmem_wait_ld();
     const float *x0 = x01, *x1 = x01 + 8;
-    float *ex0 = (float *)(sm + kOffX0), *ex1 = (float *)(sm + kOffX1);  // [e][k][j][i]
+    float *ex0 = (float *)(sm + L::kOffX0), *ex1 = (float *)(sm + L::kOffX1);  // [e][k][j][i]
     const int xrow = le * kXe + kXk * lb + 8 * la;   // as r-row (j, k) = (la, lb): x0[i] at (i, j, k)
     const int xcol = le * kXe + kXk * lb + la;       // as s-row (i, k) = (la, lb): x1[j] at (i, j, k)
     const int xown = le * kXe + 8 * lb + la;         // as t-fiber owner (i, j) = (la, lb): + kXk k
@@ -278,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
     for (int q = 0; q < 8; ++q) ex1[xcol + 8 * q] = x1[q];
     __syncthreads();
     // 4. geometry along the t-fiber of (i, j) = (la, lb), element le
-    float tt[8];
+    uint32_t tt[8];  // the t values, coded in the operand format
     {
       const bool live = le < nel;
       const int64_t e = e0 + le;
@@ -294,21 +382,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
         if (live) gm.apply(la + lb * kN1 + k * kN1 * kN1, cx[k], cw[k], xv, o3);
         // 5. r, s into their operand buffers at once (the forward MMAs are
         // done and the exchange buffers are apart), t after the loop
-        *(float *)(bufR + cm_off(lb + 8 * k + 64 * le, la, kLboR, kSboR)) = tf32_rn(o3[0]);
-        *(float *)(bufS + cm_off(la + 8 * k + 64 * le, lb, kLboS, kSboS)) = tf32_rn(o3[1]);
-        tt[k] = tf32_rn(o3[2]);
+        st_op<OP>(bufR, cm_off<ESZ>(lb + 8 * k + 64 * le, la, F::kLboR, F::kSboR), o3[0]);
+        st_op<OP>(bufS, cm_off<ESZ>(la + 8 * k + 64 * le, lb, F::kLboS, F::kSboS), o3[1]);
+        tt[k] = code<OP>(o3[2]);
       }
     }
-    *(float4 *)(bufT + cm_off(tid, 0, kLboT, kSboT)) = make_float4(tt[0], tt[1], tt[2], tt[3]);
-    *(float4 *)(bufT + cm_off(tid, 4, kLboT, kSboT)) = make_float4(tt[4], tt[5], tt[6], tt[7]);
+    st_code4<OP>(bufT, cm_off<ESZ>(tid, 0, F::kLboT, F::kSboT), tt);
+    st_code4<OP>(bufT, cm_off<ESZ>(tid, 4, F::kLboT, F::kSboT), tt + 4);
     proxy_fence();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      mma_tf32(tmem, desc(aR, kLboR, kSboR), desc(aBDT + kSboB, kLboB, kSboB), 0u);
-      mma_tf32(tmem, desc(aS, kLboS, kSboS), desc(aBDT, kLboB, kSboB), 1u);
-      mma_tf32(tmem + 16, desc(aT, kLboT, kSboT), desc(aBDT + kSboB, kLboB, kSboB), 0u);
+      mma<OP>(tmem, desc(aR, F::kLboR, F::kSboR), desc(aBDT + F::kSboB, F::kLboB, F::kSboB), 0u);
+      mma<OP>(tmem, desc(aS, F::kLboS, F::kSboS), desc(aBDT, F::kLboB, F::kSboB), 1u);
+      mma<OP>(tmem + 16, desc(aT, F::kLboT, F::kSboT), desc(aBDT + F::kSboB, F::kLboB, F::kSboB), 0u);
       commit(smem_u32(bar));
     }
     if (tid == 0 && !mbar_wait(smem_u32(bar), phase)) abort_cta = 1;
@@ -350,14 +438,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
 
 // Launch over a.E elements of order 7: kCtasPerSm CTAs per SM, persistent
 // over the tiles of two elements.
-template <int KIND>
+template <int KIND, int OP>
 cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
   const int64_t ntile = (a.E + kEPB - 1) / kEPB;
   if (ntile <= 0) return cudaSuccess;
   static int grid_cap = 0;
   if (!grid_cap) {
-    cudaError_t e = cudaFuncSetAttribute(ax_umma_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(ax_umma_kernel<KIND, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Smem<OP>::kBytes);
     int dev = 0, sms = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -366,7 +454,7 @@ cudaError_t launch_kind(const AxArgs &a, const float *Dp) {
   }
   const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
   const int64_t grid = ntile < cap ? ntile : cap;
-  ax_umma_kernel<KIND><<<(unsigned)grid, kThreads, kSmemBytes, a.stream>>>(
+  ax_umma_kernel<KIND, OP><<<(unsigned)grid, kThreads, Smem<OP>::kBytes, a.stream>>>(
       a.E, (const float *)a.geo, (const float *)a.lam, (const float *)a.X, (float *)a.Y, Dp, a.err);
   return cudaGetLastError();
 }
