@@ -276,11 +276,14 @@ def test_full_size_sampled(ax, orc, kind, prec):
     assert np.isfinite(Y).all()
 
 
+@pytest.mark.parametrize("prec,u", [("tf32", 2.0 ** -11), ("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11)])
 @pytest.mark.parametrize("kind", ["trilinear", "stored", "parallelepiped", "partial"])
-def test_tf32_tcgen05_full_size_sampled(ax, orc, kind):
-    # order 7 in TF32 runs on tcgen05 (TMEM accumulators): the order-7 sweep
+def test_tcgen05_full_size_sampled(ax, orc, kind, prec, u):
+    # order 7 in TF32, BF16 and FP16 runs on tcgen05 (TMEM accumulators; BF16
+    # and FP16 as kind::f16 with a zero second K half): the order-7 sweep
     # workload in the launch configuration the benchmark times, 256 sampled
-    # elements against the oracle at the TF32 tolerance; no wait ran out
+    # elements against the oracle at the format's tolerance (4 u); no wait
+    # ran out
     N = 7
     ex, ey, ez = inputs.sweep_box(N)
     V = inputs.parallelepiped_vertices(ex, ey, ez) if kind == "parallelepiped" else \
@@ -288,7 +291,7 @@ def test_tf32_tcgen05_full_size_sampled(ax, orc, kind):
     E = V.shape[0]
     X = inputs.element_vectors(E, N, seed=1).astype(np.float32)
     dev = torch.device("cuda:0")
-    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, "tf32")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, prec)
     Xd = torch.from_numpy(X).to(dev)
     Yd = torch.full_like(Xd, float("nan"))
     op.ax_local(Xd, Yd)
@@ -298,5 +301,5 @@ def test_tf32_tcgen05_full_size_sampled(ax, orc, kind):
     rng = np.random.default_rng(98)
     idx = np.concatenate([[0, E - 1], rng.choice(E, 254, replace=False)])
     Yref, _ = orc.axlocal_vertices(V[idx], X[idx].astype(np.float64), N)
-    assert _relerr(Y[idx], Yref) <= 4 * 2.0 ** -11
+    assert _relerr(Y[idx], Yref) <= 4 * u
     assert np.isfinite(Y).all()
