@@ -48,7 +48,7 @@ FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (meas
 # the same kernel (profiles/ax_dw_trilinear_n7_e32768_traffic.md), scaled by
 # elements to the 64x64x32 workload (traffic grows with the element count);
 # valid while the kernel's sources hash to "src".
-TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.566016e6 + 89.977856e6), "src": "70aa8f628d460494"}}
+TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.648448e6 + 89.971200e6), "src": "3cb892a186dc656a"}}
 
 
 # the sources that define the headline kernel (double-word AxLocal, N = 7)
