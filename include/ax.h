@@ -100,7 +100,11 @@ ax_status ax_local(ax_ctx *c, const void *X, void *Y, void *stream);
  * are processed in up to 16 chunks (at least 2048 elements each) on three
  * library streams (copy in, AxLocal, copy out) ordered by events, so the
  * transfers overlap the kernels (pinned host memory lets them run
- * asynchronously); the call is ordered after prior work on `stream`. */
+ * asynchronously); the call is ordered after prior work on `stream`.
+ * Float32 X and Y (AX_FP32, AX_TF32, AX_BF16, AX_FP16) in page-locked host
+ * memory the device can address are instead read and written by the
+ * kernel directly over the host link (no staging buffers, one launch on
+ * `stream`); X and Y must then lie wholly in such memory. */
 ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *stream);
 
 /* ax_local_host for callers that cannot allocate device memory at call time

@@ -338,6 +338,31 @@ ax_status ax_local_host(ax_ctx *c, const void *X_host, void *Y_host, void *strea
   const size_t word = io_word(c->c.prec), bytes = (size_t)c->c.E * c->c.n3 * word;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
+  // Float32 X and Y in page-locked host buffers the device can address
+  // (mapped memory): the kernel reads X and writes Y over the host link
+  // itself, so both directions stay busy for the whole call and no staging
+  // copies are made.  Measured on GB300 (order 7, 131072 elements): FP32
+  // 1.84 -> 1.60 ms per call, 0.98 of the link's two-way bound; the
+  // float64-IO kernels (double-word, FP64), which compute longer per byte
+  // with fewer resident warps, slowed down reading over the link (3.55 ->
+  // 4.58 ms) and keep the chunked copy pipeline below, as does other host
+  // memory.
+  if (word == 4) {
+    cudaPointerAttributes px{}, py{};
+    const bool mapped = cudaPointerGetAttributes(&px, X_host) == cudaSuccess &&
+                        cudaPointerGetAttributes(&py, Y_host) == cudaSuccess && px.type == cudaMemoryTypeHost &&
+                        py.type == cudaMemoryTypeHost && px.devicePointer && py.devicePointer;
+    (void)cudaGetLastError();  // an attribute query that failed leaves no error behind
+    if (mapped) {
+      const char *xd = (const char *)px.devicePointer;
+      char *yd = (char *)py.devicePointer;
+      if (xd < yd + bytes && yd < xd + bytes) return fail(c, AX_EINVAL, "ax_local_host: X and Y overlap");
+      e = run_ax(c, make_args(c, xd, yd, s));
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "ax_local_host");
+      return AX_OK;
+    }
+  }
   if (c->c.hbytes < bytes) {
     cudaFree(c->c.hx);
     cudaFree(c->c.hy);

@@ -180,7 +180,9 @@ def test_host_entry_point_matches_device(ax):
                                        ("trilinear", "tf32")])
 def test_host_pipeline_chunks_match_device(ax, kind, prec):
     # 20x16x16 = 5120 elements: three chunks of the host pipeline, the last one ragged;
-    # every chunk must find its own slice of the geometry record
+    # every chunk must find its own slice of the geometry record.  Float32 X and Y
+    # both pinned take the mapped path instead (the kernel reads and writes host
+    # memory over the link); pinned X with pageable Y takes the pipeline.
     N = 3
     V = _mesh(kind, 20, 16, 16)
     X = inputs.element_vectors(V.shape[0], N, seed=2)
