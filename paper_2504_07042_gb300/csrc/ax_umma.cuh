@@ -1,6 +1,7 @@
 // AxLocal with the six contractions of Algorithm 1 on the 5th-generation
-// tensor cores (tcgen05.mma kind::tf32, accumulation in tensor memory), for
-// order N = 7 (N1 = 8).
+// tensor cores (tcgen05.mma kind::tf32 for TF32 operands, kind::f16 for
+// BF16 and FP16 operands; accumulation in tensor memory), for order N = 7
+// (N1 = 8).
 //
 // A contraction along one direction is a [fibers x 8] by [8 x 8] product.
 // Two elements' 64 fibers of one direction make the M = 128 rows of one
@@ -28,9 +29,9 @@
 //   5. r, s, t into the operand buffers; the three transposed MMAs
 //   6. the three partial products are summed through shared memory by the
 //      t-fiber owners, which store Y coalesced.
-// TF32 operands: X, r, s, t are rounded to TF32 (to nearest) when staged
-// (the tensor core would otherwise drop the low mantissa bits); D is rounded
-// once.
+// Operands: X, r, s, t are rounded to the operand format (to nearest) when
+// staged (for TF32 the tensor core would otherwise drop the low mantissa
+// bits); D is rounded once per CTA.
 // Every mbarrier wait is bounded; one that runs out sets the kernel's error
 // word, and the CTA stops and frees its tensor memory.
 #pragma once
