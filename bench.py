@@ -48,7 +48,7 @@ FP64_OPS_PER_SM_CLK = 2  # FP64 FMA instructions per SM per clock on GB300 (meas
 # the same kernel (profiles/ax_dw_trilinear_n7_e32768_traffic.md), scaled by
 # elements to the 64x64x32 workload (traffic grows with the element count);
 # valid while the kernel's sources hash to "src".
-TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.648448e6 + 89.971200e6), "src": "3cb892a186dc656a"}}
+TRAFFIC = {"ax_fiber_kernel<DW, 8, 1, 1>": {"bytes": 4.0 * (140.625664e6 + 90.101504e6), "src": "396301e52c1c9ebc"}}
 
 
 # the sources that define the headline kernel (double-word AxLocal, N = 7)
@@ -357,7 +357,7 @@ def run_reference(args):
 def _detail_path(args):
     if args.detail:
         return args.detail
-    return os.path.join(ROOT, "gpurun_out", "bench_detail.json")
+    return os.path.join(ROOT, "bench_out", "bench_detail.json")
 
 
 def _write_detail(path, detail):
@@ -762,7 +762,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--detail", default=None, help="side file for the sweep and solver sections "
-                    "(default gpurun_out/bench_detail.json)")
+                    "(default bench_out/bench_detail.json)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -52,6 +52,7 @@ struct Native {
   __device__ static __forceinline__ S st(V v) { return v; }
   __device__ static __forceinline__ V cst(const C *p) { return *p; }
   __device__ static __forceinline__ V from_io(IO v) { return v; }
+  __device__ static __forceinline__ V from_io_direct(IO v) { return v; }
   __device__ static __forceinline__ IO to_io(V v) { return v; }
   __device__ static __forceinline__ V lit(double v) { return (T)v; }
   __device__ static __forceinline__ A zero() { return T(0); }
@@ -68,6 +69,7 @@ struct Native {
   __device__ static __forceinline__ V fma3(V a, V b, V c) { return fma(a, b, c); }
   __device__ static __forceinline__ V twice(V a) { return a + a; }
   __device__ static __forceinline__ IO sum3_io(V a, V b, V c) { return (a + b) + c; }
+  __device__ static __forceinline__ IO sum3_io_direct(V a, V b, V c) { return (a + b) + c; }
   __device__ static __forceinline__ V div(V a, V b) {
     if constexpr (sizeof(T) == 4)
       return __fdividef(a, b);  // 2-ulp quotient: the FP32 path's tolerance is 2e-5
@@ -100,6 +102,8 @@ struct DW {
   __device__ static __forceinline__ S st(V v) { return make_float2(v.hi, v.lo); }
   __device__ static __forceinline__ V cst(const C *p) { return dw::from_float2(*p); }
   __device__ static __forceinline__ V from_io(IO v) { return dw::from_double(v); }
+  // inside the direct range (the main kernel): no FP64-pipe instruction
+  __device__ static __forceinline__ V from_io_direct(IO v) { return dw::from_double_direct(v); }
   __device__ static __forceinline__ IO to_io(V v) { return dw::to_double(v); }
   __device__ static __forceinline__ V lit(double v) { return dw::make((float)v, 0.0f); }  // exact small literals only
   __device__ static __forceinline__ A zero() { return dw::acc_zero(); }
@@ -117,6 +121,7 @@ struct DW {
   __device__ static __forceinline__ V fma3(V a, V b, V c) { return dw::fma(a, b, c); }
   __device__ static __forceinline__ V twice(V a) { return dw::make(2.0f * a.hi, 2.0f * a.lo); }  // exact
   __device__ static __forceinline__ IO sum3_io(V a, V b, V c) { return dw::sum3_to_double(a, b, c); }
+  __device__ static __forceinline__ IO sum3_io_direct(V a, V b, V c) { return dw::sum3_to_double_direct(a, b, c); }
   __device__ static __forceinline__ V div(V a, V b) { return dw::div(a, b); }
   __device__ static __forceinline__ V neg(V a) { return dw::neg(a); }
 };
@@ -523,10 +528,13 @@ __device__ __forceinline__ int exp_field(float v) { return (__float_as_int(v) >>
 // the largest magnitude of the row, read from the upper 32 bits of the
 // float64 values (sign cleared, integer order = magnitude order): a row is
 // direct when it is all zero or its largest magnitude lies in
-// [2^-60, 2^61).  Within it the float pairs and every intermediate of the
-// product stay normal floats for element extents in [2^-20, 2^24] (checked
-// at setup); values far below their row's largest contribute below the
-// accuracy.
+// [2^-60, 2^61), and no value of it is nonzero below 2^-74.  Within it the
+// float pairs and every intermediate of the product stay normal floats for
+// element extents in [2^-20, 2^24] (checked at setup), values far below their
+// row's largest contribute below the accuracy, and X is converted by integer
+// instructions (dw::from_double_direct, whose range ends at 2^-74); Y goes
+// back the same way (dw::sum3_to_double_direct).  The fix-up kernel over the
+// other blocks converts on the FP64 pipe.
 __device__ __forceinline__ int mag_hi(double v) { return __double2hiint(v) & 0x7fffffff; }
 __device__ __forceinline__ bool row_direct(int hmax) {
   return hmax == 0 || (hmax >= ((1023 - 60) << 20) && hmax < ((1023 + 61) << 20));
@@ -552,10 +560,11 @@ __device__ __forceinline__ bool load_rows(const typename P::IO *__restrict__ src
       if (emax) v = v * pow2i(io_shift(emax[m / n3]));
     }
     if constexpr (P::kScaleIO) {
-      // each value alone is its own "row" here
+      // each value alone is its own "row" here (a nonzero value is then at
+      // least 2^-60: inside from_io_direct's range)
       if (!emax) wide |= !row_direct(mag_hi(v));
     }
-    xs[row * PITCH + (m - row * N1)] = P::st(P::from_io(v));
+    xs[row * PITCH + (m - row * N1)] = P::st(emax ? P::from_io(v) : P::from_io_direct(v));
   };
   if constexpr (n3 % VEC == 0) {
     if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
@@ -718,14 +727,20 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
         S *dst = xs + row * Sh::P;
         // SCALE 2: one row per thread (threads = EPB N1^2), row tid of element z
         const IO sc = SCALE == 2 ? (IO)pow2i(xshift) : IO(1);
-        int hmax = 0;  // SCALE 1: the row's largest magnitude (upper 32 bits)
+        int hmax = 0;       // SCALE 1: the row's largest magnitude (upper 32 bits)
+        bool tiny = false;  // SCALE 1: a nonzero value below from_io_direct's range
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
           const IO v = X[src + i];
-          if constexpr (SCALE == 1) hmax = max(hmax, mag_hi(v));
-          dst[i] = P::st(P::from_io(SCALE == 2 ? v * sc : v));
+          if constexpr (SCALE == 1) {
+            hmax = max(hmax, mag_hi(v));
+            if constexpr (P::kScaleIO) tiny |= dw::tiny_nonzero((unsigned)mag_hi(v));
+            dst[i] = P::st(P::from_io_direct(v));
+          } else {
+            dst[i] = P::st(P::from_io(SCALE == 2 ? v * sc : v));
+          }
         }
-        if constexpr (SCALE == 1) wide |= !row_direct(hmax);
+        if constexpr (SCALE == 1) wide |= tiny || !row_direct(hmax);
       }
     }
     if constexpr (GW > 0) {
@@ -829,7 +844,8 @@ __device__ __forceinline__ bool fiber_block(const FiberSmem<P, N1, KIND, EM, EPB
       for (int k = 0; k < N1; ++k) {
         const int sidx = ft + k * str_t;
         const V ytk = kYtRegs ? yt[kYtRegs ? k : 0] : P::ld(x_e + sidx);
-        ye[k * N1 * N1] = P::sum3_io(ytk, P::ld(r_e + sidx), P::ld(s_e + sidx));
+        const V yr = P::ld(r_e + sidx), ys = P::ld(s_e + sidx);
+        ye[k * N1 * N1] = SCALE == 1 ? P::sum3_io_direct(ytk, yr, ys) : P::sum3_io(ytk, yr, ys);
       }
       if constexpr (SCALE == 2) {
         // undo the element's input shift on the values just stored (exact)

@@ -168,5 +168,50 @@ __device__ __forceinline__ double sum3_to_double(dw a, dw b, dw c) {
   return (double)s2.hi + (double)lo;
 }
 
+// The same conversions without FP64-pipe instructions, for values inside a
+// kernel's direct range.  The forms above spend four (float64 -> pair) and
+// two (pair -> float64, besides the last addition) instructions per value on
+// the FP64 pipe, which GB300 runs at 1/64 of the FP32 rate; here the words
+// are assembled by integer instructions on the IEEE-754 bit fields.
+//
+// float64 -> pair: hi holds the leading 24 significand bits of v (truncated:
+// the exponent re-biased from 1023 to 127, the top 23 fraction bits shifted
+// into place), lo the 29 fraction bits below them, converted as an integer
+// with one rounding (cvt.rn.f32.u32) and scaled by their weight
+// 2^(E - 1075), E the biased exponent of v (a product by a power of two:
+// exact).  |hi + lo - v| <= 2^-48 |v|, as for from_double.  Valid for |v| in
+// [2^-74, 2^128), where both words are normal floats; smaller magnitudes give
+// 0 (the caller reports them: tiny_nonzero), larger ones, infinities and NaNs
+// meaningless words (the caller routes them to from_double).
+__device__ __forceinline__ dw from_double_direct(double v) {
+  const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+  const unsigned a = hw & 0x7fffffffu;
+  const unsigned hb = __funnelshift_l(lw, a - (896u << 20), 3) | (hw & 0x80000000u);
+  const float scale = __uint_as_float((hb & 0xff800000u) - (52u << 23));  // +-2^(E - 1075)
+  const float lo = __fmul_rn(__uint2float_rn(lw & 0x1fffffffu), scale);
+  const bool tiny = a < (949u << 20);  // |v| < 2^-74
+  return dw{tiny ? 0.0f : __uint_as_float(hb), tiny ? 0.0f : lo};
+}
+// v is nonzero and below from_double_direct's range (flushed to 0 there);
+// a = upper 32 bits of |v|
+__device__ __forceinline__ bool tiny_nonzero(unsigned a) { return a - 1u < (949u << 20) - 1u; }
+// float -> float64 by integer instructions: exact for normal floats and
+// zero; subnormal floats (below 2^-126) give 0, infinities and NaNs
+// meaningless values
+__device__ __forceinline__ double float_to_double_direct(float f) {
+  const unsigned b = __float_as_uint(f), a = b & 0x7fffffffu;
+  const bool z = a < 0x00800000u;
+  const unsigned hw = ((a >> 3) + (896u << 20)) | (b & 0x80000000u);
+  return __hiloint2double(z ? 0 : (int)hw, z ? 0 : (int)(b << 29));
+}
+// sum3_to_double with the two float -> float64 conversions above: one
+// FP64-pipe instruction (the last addition) per value
+__device__ __forceinline__ double sum3_to_double_direct(dw a, dw b, dw c) {
+  const dw s1 = two_sum(a.hi, b.hi);
+  const dw s2 = two_sum(s1.hi, c.hi);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), c.lo), __fadd_rn(s1.lo, s2.lo));
+  return float_to_double_direct(s2.hi) + float_to_double_direct(lo);
+}
+
 }  // namespace dw
 }  // namespace ax

@@ -25,6 +25,8 @@ int main() {
   std::uniform_int_distribution<int> Ex(-20, 20);
   const LD unit = std::ldexp((LD)1, -47);
   LD e_two = 0, e_mul = 0, e_mac = 0, e_fma = 0, e_sum = 0, e_lazy = 0, e_div = 0, e_conv = 0, e_s3 = 0, e_add = 0;
+  LD e_convd = 0, e_s3d = 0;
+  long bad_direct = 0;  // cases the FP64-pipe-free conversions get wrong (must stay 0)
   auto upd = [](LD &m, LD err, LD scale) {
     const LD r = err / (scale > 0 ? scale : 1);
     if (r > m) m = r;
@@ -60,9 +62,50 @@ int main() {
     const double v = (double)(U(g) * sa);
     upd(e_conv, fabsl((LD)to_double(from_double(v)) - (LD)v), fabsl((LD)v));
     upd(e_s3, fabsl((LD)sum3_to_double(a, b, c) - (A + B + C)), fabsl(A) + fabsl(B) + fabsl(C));
+    upd(e_s3d, fabsl((LD)sum3_to_double_direct(a, b, c) - (A + B + C)), fabsl(A) + fabsl(B) + fabsl(C));
+    // float64 -> pair without the FP64 pipe, over its whole range [2^-74, 2^128)
+    // (random 53-bit significands, both signs)
+    {
+      const int ex = std::uniform_int_distribution<int>(-74, 127)(g);
+      const double w = std::ldexp(std::uniform_real_distribution<double>(1.0, 2.0)(g), ex) * (U(g) < 0 ? -1 : 1);
+      const dw p2 = from_double_direct(w);
+      upd(e_convd, fabsl((LD)p2.hi + (LD)p2.lo - (LD)w), fabsl((LD)w));
+      if (std::fabs(p2.lo) >= std::fabs(p2.hi) * 0x1p-23f) ++bad_direct;  // |lo| < ulp(hi)
+      if (tiny_nonzero((unsigned)__double2hiint(w) & 0x7fffffffu)) ++bad_direct;
+      // float -> float64 exact on normal floats
+      const float f = (float)w;
+      if (std::isnormal(f) && float_to_double_direct(f) != (double)f) ++bad_direct;
+    }
   }
+  // below the range: flushed to 0 and reported, except below 2^-1042, where the
+  // upper 32 bits (all the range tests read) are zero and the value counts as
+  // a zero; zeros of either sign pass as 0
+  for (int ex = -1074; ex < -74; ++ex) {
+    if (ex < -1042) {
+      const dw p2 = from_double_direct(std::ldexp(1.5, ex));
+      if (p2.hi != 0.0f || p2.lo != 0.0f) ++bad_direct;
+      continue;
+    }
+    const double w = std::ldexp(1.5, ex);
+    const dw p2 = from_double_direct(w);
+    if (p2.hi != 0.0f || p2.lo != 0.0f) ++bad_direct;
+    if (!tiny_nonzero((unsigned)__double2hiint(w) & 0x7fffffffu)) ++bad_direct;
+  }
+  for (double z : {0.0, -0.0}) {
+    const dw p2 = from_double_direct(z);
+    if (p2.hi != 0.0f || p2.lo != 0.0f || tiny_nonzero((unsigned)__double2hiint(z) & 0x7fffffffu)) ++bad_direct;
+    if (float_to_double_direct((float)z) != 0.0) ++bad_direct;
+  }
+  // exact powers of two and the largest significand at both ends of the range
+  for (double w : {0x1p-74, 0x1.fffffffffffffp-74, 0x1p127, 0x1.fffffffffffffp127, 1.0, -1.0, 0x1.fffffffffffffp0}) {
+    const dw p2 = from_double_direct(w);
+    upd(e_convd, fabsl((LD)p2.hi + (LD)p2.lo - (LD)w), fabsl((LD)w));
+  }
+  // float subnormals go to 0
+  if (float_to_double_direct(0x1p-130f) != 0.0 || float_to_double_direct(-0x1p-149f) != 0.0) ++bad_direct;
   std::printf("two_sum %.3Lg\nadd %.3Lg\nmul %.3Lg\nfma %.3Lg\nmac %.3Lg\nacc_sum %.3Lg\nlazy %.3Lg\ndiv %.3Lg\nconv %.3Lg\nsum3 %.3Lg\n",
               e_two, e_add / unit, e_mul / unit, e_fma / unit, e_mac / unit, e_sum / unit, e_lazy / unit, e_div / unit,
               e_conv / unit, e_s3 / unit);
+  std::printf("conv_direct %.3Lg\nsum3_direct %.3Lg\nbad_direct %ld\n", e_convd / unit, e_s3d / unit, bad_direct);
   return 0;
 }

@@ -20,7 +20,7 @@ import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BOUNDS = {"two_sum": 0.0, "add": 2.0, "mul": 2.0, "fma": 4.0, "mac": 8.0, "acc_sum": 8.0, "lazy": 8.0,
-          "div": 8.0, "conv": 0.5, "sum3": 4.0}
+          "div": 8.0, "conv": 0.5, "sum3": 4.0, "conv_direct": 0.5, "sum3_direct": 4.0, "bad_direct": 0.0}
 
 
 def test_double_word_building_blocks(tmp_path):

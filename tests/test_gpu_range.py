@@ -78,6 +78,25 @@ def test_x_mixed_scales_per_element(ax, orc, kind):
             assert np.max(np.abs(Y[e] - Yref[e])) <= 1e-12 * m, e
 
 
+@pytest.mark.parametrize("N", [5, 7, 15])
+def test_x_entries_below_direct_conversion(ax, orc, N):
+    # elements of magnitude 2^-58 with single entries near 2^-76 and 2^-72:
+    # the main kernel converts X to float pairs by integer instructions down
+    # to 2^-74 only; an entry below that sends its block through the scaled
+    # pass (were it flushed to zero, Y would be off by about 2^-18 relative)
+    V = _mesh("trilinear", n=3)
+    E = V.shape[0]
+    X = inputs.element_vectors(E, N, seed=4) * 2.0 ** -58
+    rng = np.random.default_rng(5)
+    for e in range(E):
+        idx = rng.choice(X.shape[1], 6, replace=False)
+        X[e, idx] = 2.0 ** rng.choice([-76.0, -72.0], 6) * rng.uniform(1.0, 2.0, 6) * rng.choice([-1.0, 1.0], 6)
+    Y = _run(ax, V, X, N, "trilinear", "f64dw")
+    Yref, _ = orc.axlocal_vertices(V, X, N)
+    for e in range(E):
+        assert np.max(np.abs(Y[e] - Yref[e])) <= 1e-12 * np.max(np.abs(Yref[e])), e
+
+
 @pytest.mark.parametrize("mscale", [1e-4, 1e-5, 1e7])
 @pytest.mark.parametrize("kind", ["stored", "trilinear", "parallelepiped", "partial"])
 @pytest.mark.parametrize("N", [3, 7])
