@@ -185,6 +185,20 @@ def _time_launches(torch, fn, steps, warmup, stream):
     return t0.elapsed_time(t1) / steps  # ms
 
 
+def _median_launch_ms(torch, fn, launches, warmup, stream):
+    """Median over `launches` launches, each timed alone by CUDA events on the
+    launching stream, after `warmup` untimed launches."""
+    for _ in range(warmup):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(launches)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
 def reduce_max_ms(torch, ms, device):
     """Max over ranks of a per-rank time (ms); identity on one process."""
     import torch.distributed as dist
@@ -283,6 +297,20 @@ def cpu_oracle_rate(seconds=10.0, N=HEADLINE_N):
             break
     return (reps * m * n3 / dt / 1e9, oracle.num_threads(),
             "%d pass(es) over the first %d of %d elements (%.1f s)" % (reps, m, V.shape[0], dt))
+
+
+def host_cpu():
+    """The host's CPU model and logical CPU count (lscpu where present)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model, "logical_cpus": os.cpu_count()}
 
 
 def cpu_oracle_sweep(seconds=1.5):
@@ -469,6 +497,7 @@ def run(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                                 "single_thread_value": rate1}
         detail["cpu_baseline_single_thread"] = {"value": rate1, "unit": UNIT, "sample": sample1}
+        detail["host_cpu"] = host_cpu()
         if not args.no_sweep:
             detail["cpu_oracle_sweep"] = cpu_oracle_sweep()
         line["detail"] = os.path.relpath(_write_detail(_detail_path(args), detail) or "", ROOT)
@@ -730,7 +759,8 @@ def run_learned(ax, torch, dev):
 
 
 def run_sweep(ax, torch, dev, hbm, sm_mhz, sms=SM_COUNT):
-    """Per-N GDOF/s and roofline fraction, recompute vs stored, per precision."""
+    """Per-N GDOF/s and roofline fraction, recompute vs stored, per precision:
+    the median of 20 launches, each timed alone, after 3 warm-up launches."""
     out = []
     stream = torch.cuda.current_stream()
     for N in (3, 5, 7, 9, 11, 15):
@@ -741,7 +771,7 @@ def run_sweep(ax, torch, dev, hbm, sm_mhz, sms=SM_COUNT):
                         continue  # tensor-core contractions: the recompute kinds only
                     op, X, Y, _ = _build_case(ax, torch, dev, N, kind, prec, mesh)
                     info = op.ax_query()
-                    ms = _time_launches(torch, lambda: op.ax_local(X, Y, stream), 5, 2, stream)
+                    ms = _median_launch_ms(torch, lambda: op.ax_local(X, Y, stream), 20, 3, stream)
                     roof = _roofline(info, ms, sm_mhz, hbm, sms)
                     out.append({"N": N, "mesh": mesh, "kind": kind, "prec": prec, "E": op.E,
                                 "gdofs": op.E * op.n3 / (ms * 1e-3) / 1e9, "ms": ms, "bound": roof["bound"],
