@@ -295,6 +295,19 @@ cudaError_t launch_tc_kind(const AxArgs &a, const float *Dp) {
 
 template <int MODE, int N1>
 cudaError_t launch_tc_n(const AxArgs &a, const float *Dp) {
+  if constexpr (N1 == 4 || N1 == 6 || N1 == 10) {
+    // orders 3, 5, 9: the tcgen05 kernel sized to the order (tile variant 1
+    // selects the mma.sync kernel below)
+    if (a.tile != 1) {
+      switch (a.kind) {
+        case AX_GEOM_STORED: return umma::launch_gen<N1, AX_GEOM_STORED, MODE>(a, Dp);
+        case AX_GEOM_TRILINEAR: return umma::launch_gen<N1, AX_GEOM_TRILINEAR, MODE>(a, Dp);
+        case AX_GEOM_PARALLELEPIPED: return umma::launch_gen<N1, AX_GEOM_PARALLELEPIPED, MODE>(a, Dp);
+        case AX_GEOM_TRILINEAR_PARTIAL: return umma::launch_gen<N1, AX_GEOM_TRILINEAR_PARTIAL, MODE>(a, Dp);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
   if constexpr (N1 == 8) {
     // order 7: tcgen05 in every format (operand format = MODE; tile variant 1
     // selects the mma.sync kernel below)

@@ -437,6 +437,293 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Orders N = 3, 5, 9 (N1 = 4, 6, 10): the same six-MMA structure with the
+// tile sized to the order.  A tile is EPB = 128 / N1^2 elements (8, 3, 1),
+// whose ROWS = EPB N1^2 fibers of a direction (128, 108, 100) are the MMA
+// rows in use; the other rows stay zero and their results are not read.
+// The contraction index K is padded with zeros to whole MMA instructions
+// (TF32: K = 8 per instruction, the 16-bit formats K = 16): the operand
+// buffers are zeroed once per CTA and only their data positions are written
+// afterwards, so every pad holds zero.  N1 <= 8: the r and s products share
+// one 16-column accumulator (the D windows of the order-7 kernel) and t has
+// the next (32 columns); N1 = 10: D fills rows 0-9 of a 16-row B buffer and
+// each direction has its own 16-column accumulator (64 columns).  Operand
+// buffers are dense core-matrix layouts (K core columns 128 bytes apart)
+// with 16 bytes of padding per 8-row group; X is read with scalar coalesced
+// loads.  Thread L is row L of every direction: r-fiber (j, k, e), s-fiber
+// (i, k, e) and t-fiber (i, j, e) with (a, b, e) = (L % N1, L / N1 % N1,
+// L / N1^2); x0 and x1 reach the t-fiber owners through the exchange
+// buffers [e][k][j][i] (k pitch XK), as in the order-7 kernel.
+// ---------------------------------------------------------------------------
+template <int N1, int OP>
+struct GShape {
+  static constexpr int F = N1 * N1, EPB = 128 / F, ROWS = EPB * F, N3 = N1 * N1 * N1, TN = EPB * N3;
+  static constexpr int ESZ = OP == 0 ? 4 : 2, PER = 16 / ESZ;   // bytes per value, K values per core row
+  static constexpr int KI = OP == 0 ? 8 : 16;                   // K per MMA instruction
+  static constexpr int NI = (N1 + KI - 1) / KI;                 // instructions per contraction
+  static constexpr int NC = NI * KI / PER;                      // K core columns of every operand buffer
+  static constexpr uint32_t LBO = 128, SBO = NC * 128 + 16, ABYTES = 16 * SBO;
+  static constexpr bool SPLIT = N1 > 8;                          // one accumulator per direction
+  static constexpr int BROWS = SPLIT ? 16 : 24, BROW0 = SPLIT ? 0 : 8;  // B buffer rows, first row of D
+  static constexpr uint32_t SBOB = NC * 128, BBYTES = (BROWS / 8) * SBOB;
+  static constexpr int TCOLS = SPLIT ? 64 : 32;                  // tensor-memory columns
+  // exchange k pitch: F, or F + 4 where F is an odd multiple of 16, so that
+  // the k pitch is 4 times an odd number modulo 32 (the stride-XK writes of
+  // a warp then spread over the banks)
+  static constexpr int XK = F + ((F % 32) == 16 ? 4 : 0), XE = N1 * XK, XF = EPB * XE;
+  static constexpr int LOADS = (TN + 127) / 128;                 // X values per thread and tile
+  static constexpr uint32_t OFF_R = 0, OFF_S = ABYTES, OFF_T = 2 * ABYTES, OFF_X0 = 3 * ABYTES,
+                            OFF_X1 = OFF_X0 + (uint32_t)(XF * 4 + 15) / 16 * 16,
+                            OFF_BD = OFF_X1 + (uint32_t)(XF * 4 + 15) / 16 * 16, OFF_BDT = OFF_BD + BBYTES,
+                            OFF_GEO = OFF_BDT + BBYTES, BYTES = OFF_GEO + EPB * kVertexWords * 4 + 64;
+  static_assert(EPB >= 1 && N1 <= 16 - BROW0 && N1 <= 16, "tile shape");
+  static_assert(ABYTES % 16 == 0 && BBYTES % 16 == 0, "16-byte aligned operand buffers");
+};
+// resident CTAs per SM: as the order-7 kernel below N1 = 10; at N1 = 10 the
+// thread holds three rows of 10 values, so four CTAs (up to 128 registers)
+template <int N1, int KIND>
+constexpr int kCtasGen = N1 > 8 ? 4 : kCtasPerSm<KIND>;
+
+template <int N1, int KIND, int OP>
+__global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
+    ax_umma_gen_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
+                       const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
+                       int *__restrict__ err) {
+  using P = fiber::Native<float>;
+  using G = GShape<N1, OP>;
+  constexpr int ESZ = G::ESZ, F = G::F, EPB = G::EPB, N3 = G::N3;
+  constexpr int GW = fiber::GeoWords<KIND>::value;
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char *bufR = sm + G::OFF_R, *bufS = sm + G::OFF_S, *bufT = sm + G::OFF_T;
+  float *ex0 = (float *)(sm + G::OFF_X0), *ex1 = (float *)(sm + G::OFF_X1);
+  float *sgeo = (float *)(sm + G::OFF_GEO);
+  uint64_t *bar = (uint64_t *)(sm + G::OFF_GEO + EPB * kVertexWords * 4);
+  uint32_t *tslot = (uint32_t *)(bar + 1);
+  __shared__ int abort_cta;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const float *cw = fiber::c_w + tab_off_v(N1);
+  const float *cx = fiber::c_x + tab_off_v(N1);
+
+  // the three operand buffers zeroed (pads stay zero), then D and D^T in
+  // their B buffers (rows a, K = m and rows m, K = a), zero elsewhere
+  for (uint32_t q = tid; q < 3 * G::ABYTES / 16; q += kThreads) ((uint4 *)sm)[q] = make_uint4(0u, 0u, 0u, 0u);
+  constexpr int KB = G::NC * G::PER;  // K positions per B row
+  for (int q = tid; q < 2 * G::BROWS * KB; q += kThreads) {
+    const int which = q / (G::BROWS * KB), row = (q % (G::BROWS * KB)) / KB, k = q % KB, a = row - G::BROW0;
+    float v = 0.0f;
+    if (a >= 0 && a < N1 && k < N1) v = which == 0 ? Dp[a * N1 + k] : Dp[k * N1 + a];
+    st_op<OP>(sm + (which == 0 ? G::OFF_BD : G::OFF_BDT), cm_off<ESZ>(row, k, G::LBO, G::SBOB), v);
+  }
+  if (tid == 0) {
+    abort_cta = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(G::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t aR = smem_u32(bufR), aS = smem_u32(bufS), aT = smem_u32(bufT);
+  const uint32_t aBD = smem_u32(sm + G::OFF_BD), aBDT = smem_u32(sm + G::OFF_BDT);
+  const int la = tid % N1, lb = (tid / N1) % N1, le = tid / F;
+  const bool row_in_use = tid < G::ROWS;
+  uint32_t phase = 0;
+  constexpr uint32_t kStepA = (G::KI / G::PER) * G::LBO;  // bytes of K per instruction (A and B alike)
+
+  // the six (forward or transposed) contractions of a tile, issued by one thread
+  auto issue = [&](uint32_t aB) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if constexpr (!G::SPLIT) {
+      mma<OP>(tmem, desc(aR, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
+      mma<OP>(tmem, desc(aS, G::LBO, G::SBO), desc(aB, G::LBO, G::SBOB), 1u);
+      mma<OP>(tmem + 16, desc(aT, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
+    } else {
+      const uint32_t aA[3] = {aR, aS, aT};
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int q = 0; q < G::NI; ++q)
+          mma<OP>(tmem + 16 * d, desc(aA[d] + q * kStepA, G::LBO, G::SBO), desc(aB + q * kStepA, G::LBO, G::SBOB),
+                  q > 0 ? 1u : 0u);
+    }
+    commit(smem_u32(bar));
+  };
+  // this thread's TMEM row: the r-, s- and t-direction results (N1 values each)
+  auto read_rows = [&](float v0[N1], float v1[N1], float v2[N1]) {
+    if constexpr (!G::SPLIT) {
+      float a16[16], a8[8];
+      tmem_ld16(tlane + 0, a16);
+      tmem_ld8(tlane + 16, a8);
+      tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        v0[q] = a16[q];
+        v1[q] = a16[8 + q];
+        v2[q] = a8[q];
+      }
+    } else {
+      float a[16], b[16], c[16];
+      tmem_ld16(tlane + 0, a);
+      tmem_ld16(tlane + 16, b);
+      tmem_ld16(tlane + 32, c);
+      tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        v0[q] = a[q];
+        v1[q] = b[q];
+        v2[q] = c[q];
+      }
+    }
+  };
+  // r-row values (over i) and s-row values (over j) to the t-fiber owners
+  const int xrow = le * G::XE + G::XK * lb + N1 * la;  // r-row (j, k) = (la, lb): value i at + i
+  const int xcol = le * G::XE + G::XK * lb + la;       // s-row (i, k) = (la, lb): value j at + N1 j
+  const int xown = le * G::XE + N1 * lb + la;          // t-fiber owner (i, j) = (la, lb): node k at + XK k
+  auto exchange = [&](const float v0[N1], const float v1[N1]) {
+    if (row_in_use) {
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        ex0[xrow + q] = v0[q];
+        ex1[xcol + N1 * q] = v1[q];
+      }
+    }
+  };
+
+  const int64_t ntile = (E + EPB - 1) / EPB;
+  auto load_x = [&](int64_t tt, float xv[G::LOADS]) {
+    const int64_t b0 = tt * EPB;
+    const int64_t nv = tt < ntile ? ((E - b0) < EPB ? (E - b0) : EPB) * N3 : 0;
+#pragma unroll
+    for (int s2 = 0; s2 < G::LOADS; ++s2) {
+      const int m = tid + kThreads * s2;
+      xv[s2] = m < nv ? X[b0 * N3 + m] : 0.0f;
+    }
+  };
+  float xnext[G::LOADS];
+  load_x(blockIdx.x, xnext);
+  for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const int64_t e0 = t * EPB;
+    const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+    // 1. X into the three operand buffers (zeros beyond the last element)
+#pragma unroll
+    for (int s2 = 0; s2 < G::LOADS; ++s2) {
+      const int m = tid + kThreads * s2;
+      if (m < G::TN) {
+        const int e = m / N3, rem = m % N3, i = rem % N1, j = (rem / N1) % N1, k = rem / F;
+        const uint32_t c = code<OP>(xnext[s2]);
+        st_code<OP>(bufR, cm_off<ESZ>(j + N1 * k + F * e, i, G::LBO, G::SBO), c);
+        st_code<OP>(bufS, cm_off<ESZ>(i + N1 * k + F * e, j, G::LBO, G::SBO), c);
+        st_code<OP>(bufT, cm_off<ESZ>(i + N1 * j + F * e, k, G::LBO, G::SBO), c);
+      }
+    }
+    if constexpr (GW > 0) {
+      for (int m = tid; m < nel * GW; m += kThreads) sgeo[m] = geo[e0 * GW + m];
+    }
+    load_x(t + gridDim.x, xnext);  // the next tile's X, in flight meanwhile
+    proxy_fence();
+    __syncthreads();
+    // 2. forward MMAs; thread 0 waits for them (bounded), the others sleep in the barrier
+    if (tid == 0 && !abort_cta) issue(aBD);
+    if (tid == 0 && !mbar_wait(smem_u32(bar), phase)) abort_cta = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (abort_cta) {
+      if (tid == 0) mbar_wait(smem_u32(bar), phase);  // bounded: the MMAs in flight before TMEM is freed
+      break;
+    }
+    phase ^= 1u;
+    // 3. rows out of TMEM; x0 and x1 to the t-fiber owners
+    float x0[N1], x1[N1], x2[N1];
+    read_rows(x0, x1, x2);
+    exchange(x0, x1);
+    __syncthreads();
+    // 4. geometry along the t-fiber of (i, j) = (la, lb), element le; 5. r, s, t into the operand buffers
+    if (row_in_use) {
+      const bool live = le < nel;
+      const int64_t e = e0 + le;
+      fiber::Geometry<P, N1, KIND> gm;
+      gm.template prologue<false>(sgeo + le * (GW > 0 ? GW : 1), cx, cw, la, lb,
+                                  (KIND == AX_GEOM_STORED && live) ? geo + e * 7 * N3 : nullptr,
+                                  (KIND == AX_GEOM_TRILINEAR_PARTIAL && live) ? lam + e * N3 : nullptr, nullptr);
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const int o = xown + G::XK * k;
+        const float xv[3] = {ex0[o], ex1[o], x2[k]};
+        float o3[3] = {0.f, 0.f, 0.f};
+        if (live) gm.apply(la + lb * N1 + k * F, cx[k], cw[k], xv, o3);
+        st_op<OP>(bufR, cm_off<ESZ>(lb + N1 * k + F * le, la, G::LBO, G::SBO), o3[0]);
+        st_op<OP>(bufS, cm_off<ESZ>(la + N1 * k + F * le, lb, G::LBO, G::SBO), o3[1]);
+        st_op<OP>(bufT, cm_off<ESZ>(tid, k, G::LBO, G::SBO), o3[2]);
+      }
+    }
+    proxy_fence();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) issue(aBDT);
+    if (tid == 0 && !mbar_wait(smem_u32(bar), phase)) abort_cta = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (abort_cta) {
+      if (tid == 0) mbar_wait(smem_u32(bar), phase);
+      break;
+    }
+    phase ^= 1u;
+    // 6. Y = Y_r + Y_s + Y_t
+    float yr[N1], ys[N1], yt[N1];
+    read_rows(yr, ys, yt);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    exchange(yr, ys);
+    __syncthreads();
+    if (row_in_use && le < nel) {
+      float *ye = Y + (e0 + le) * N3 + la + N1 * lb;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const int o = xown + G::XK * k;
+        ye[F * k] = ex0[o] + ex1[o] + yt[k];
+      }
+    }
+    // no barrier here: the next tile writes the operand buffers (free since
+    // the MMA wait) and its exchange only after two more barriers
+  }
+  if (tid == 0 && abort_cta && err) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::TCOLS) : "memory");
+}
+
+// Launch over a.E elements of order N1 - 1 (N1 = 4, 6, 10): kCtasGen CTAs
+// per SM, persistent over the tiles.
+template <int N1, int KIND, int OP>
+cudaError_t launch_gen(const AxArgs &a, const float *Dp) {
+  using G = GShape<N1, OP>;
+  const int64_t ntile = (a.E + G::EPB - 1) / G::EPB;
+  if (ntile <= 0) return cudaSuccess;
+  static int grid_cap = 0;
+  if (!grid_cap) {
+    cudaError_t e = cudaFuncSetAttribute(ax_umma_gen_kernel<N1, KIND, OP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid_cap = kCtasGen<N1, KIND> * sms;
+  }
+  const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
+  const int64_t grid = ntile < cap ? ntile : cap;
+  ax_umma_gen_kernel<N1, KIND, OP><<<(unsigned)grid, kThreads, G::BYTES, a.stream>>>(
+      a.E, (const float *)a.geo, (const float *)a.lam, (const float *)a.X, (float *)a.Y, Dp, a.err);
+  return cudaGetLastError();
+}
+
 // Launch over a.E elements of order 7: kCtasPerSm CTAs per SM, persistent
 // over the tiles of two elements.
 template <int KIND, int OP>
