@@ -295,9 +295,9 @@ cudaError_t launch_tc_kind(const AxArgs &a, const float *Dp) {
 
 template <int MODE, int N1>
 cudaError_t launch_tc_n(const AxArgs &a, const float *Dp) {
-  if constexpr (N1 == 4 || N1 == 6 || N1 == 10) {
-    // orders 3, 5, 9: the tcgen05 kernel sized to the order (tile variant 1
-    // selects the mma.sync kernel below)
+  if constexpr (N1 >= 2 && N1 <= 11 && N1 != 8) {
+    // orders 1-10 but 7: the tcgen05 kernel sized to the order (tile
+    // variant 1 selects the mma.sync kernel below)
     if (a.tile != 1) {
       switch (a.kind) {
         case AX_GEOM_STORED: return umma::launch_gen<N1, AX_GEOM_STORED, MODE>(a, Dp);

@@ -438,17 +438,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
 }
 
 // ---------------------------------------------------------------------------
-// Orders N = 3, 5, 9 (N1 = 4, 6, 10): the same six-MMA structure with the
-// tile sized to the order.  A tile is EPB = 128 / N1^2 elements (8, 3, 1),
-// whose ROWS = EPB N1^2 fibers of a direction (128, 108, 100) are the MMA
-// rows in use; the other rows stay zero and their results are not read.
+// Orders N = 1..10 but 7 (N1 = 2..11): the same six-MMA structure with the
+// tile sized to the order.  A tile is EPB = 128 / N1^2 elements (N1 = 4, 6,
+// 10: 8, 3, 1), whose ROWS = EPB N1^2 fibers of a direction (128, 108, 100)
+// are the MMA rows in use; the other rows stay zero and their results are
+// not read.
 // The contraction index K is padded with zeros to whole MMA instructions
 // (TF32: K = 8 per instruction, the 16-bit formats K = 16): the operand
 // buffers are zeroed once per CTA and only their data positions are written
 // afterwards, so every pad holds zero.  N1 <= 8: the r and s products share
 // one 16-column accumulator (the D windows of the order-7 kernel) and t has
-// the next (32 columns); N1 = 10: D fills rows 0-9 of a 16-row B buffer and
-// each direction has its own 16-column accumulator (64 columns).  Operand
+// the next (32 columns); N1 > 8: D fills rows 0..N1-1 of a 16-row B buffer
+// and each direction has its own 16-column accumulator (64 columns).  Operand
 // buffers are dense core-matrix layouts (K core columns 128 bytes apart)
 // with 16 bytes of padding per 8-row group; X is read with scalar coalesced
 // loads.  Thread L is row L of every direction: r-fiber (j, k, e), s-fiber
@@ -480,8 +481,8 @@ struct GShape {
   static_assert(EPB >= 1 && N1 <= 16 - BROW0 && N1 <= 16, "tile shape");
   static_assert(ABYTES % 16 == 0 && BBYTES % 16 == 0, "16-byte aligned operand buffers");
 };
-// resident CTAs per SM: as the order-7 kernel below N1 = 10; at N1 = 10 the
-// thread holds three rows of 10 values, so four CTAs (up to 128 registers)
+// resident CTAs per SM: as the order-7 kernel up to N1 = 8; above, a thread
+// holds three rows of N1 values, so four CTAs (up to 128 registers)
 template <int N1, int KIND>
 constexpr int kCtasGen = N1 > 8 ? 4 : kCtasPerSm<KIND>;
 
@@ -700,8 +701,8 @@ __global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G::TCOLS) : "memory");
 }
 
-// Launch over a.E elements of order N1 - 1 (N1 = 4, 6, 10): kCtasGen CTAs
-// per SM, persistent over the tiles.
+// Launch over a.E elements of order N1 - 1: kCtasGen CTAs per SM,
+// persistent over the tiles.
 template <int N1, int KIND, int OP>
 cudaError_t launch_gen(const AxArgs &a, const float *Dp) {
   using G = GShape<N1, OP>;
