@@ -438,11 +438,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
 }
 
 // ---------------------------------------------------------------------------
-// Orders N = 1..10 but 7 (N1 = 2..11): the same six-MMA structure with the
+// Orders N = 1..15 but 7 (N1 = 2..16): the same six-MMA structure with the
 // tile sized to the order.  A tile is EPB = 128 / N1^2 elements (N1 = 4, 6,
-// 10: 8, 3, 1), whose ROWS = EPB N1^2 fibers of a direction (128, 108, 100)
-// are the MMA rows in use; the other rows stay zero and their results are
-// not read.
+// 10: 8, 3, 1; one above N1 = 11), whose ROWS = EPB N1^2 fibers of a
+// direction (128, 108, 100; 144 to 256 above N1 = 11) are the MMA rows in
+// use, in one or two 128-row MMA blocks with one thread per row (two
+// blocks: 256 threads, the second block's accumulators CPB columns to the
+// right in the same TMEM lanes); unused rows stay zero and their results
+// are not read.
 // The contraction index K is padded with zeros to whole MMA instructions
 // (TF32: K = 8 per instruction, the 16-bit formats K = 16): the operand
 // buffers are zeroed once per CTA and only their data positions are written
@@ -459,21 +462,24 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
 // ---------------------------------------------------------------------------
 template <int N1, int OP>
 struct GShape {
-  static constexpr int F = N1 * N1, EPB = 128 / F, ROWS = EPB * F, N3 = N1 * N1 * N1, TN = EPB * N3;
+  static constexpr int F = N1 * N1, EPB = F > 128 ? 1 : 128 / F, ROWS = EPB * F, N3 = N1 * N1 * N1, TN = EPB * N3;
+  static constexpr int MB = (ROWS + 127) / 128;                // 128-row MMA blocks (two above N1 = 11)
+  static constexpr int THREADS = 128 * MB;                      // one thread per row
   static constexpr int ESZ = OP == 0 ? 4 : 2, PER = 16 / ESZ;   // bytes per value, K values per core row
   static constexpr int KI = OP == 0 ? 8 : 16;                   // K per MMA instruction
   static constexpr int NI = (N1 + KI - 1) / KI;                 // instructions per contraction
   static constexpr int NC = NI * KI / PER;                      // K core columns of every operand buffer
-  static constexpr uint32_t LBO = 128, SBO = NC * 128 + 16, ABYTES = 16 * SBO;
+  static constexpr uint32_t LBO = 128, SBO = NC * 128 + 16, ABYTES = 16 * MB * SBO;
   static constexpr bool SPLIT = N1 > 8;                          // one accumulator per direction
   static constexpr int BROWS = SPLIT ? 16 : 24, BROW0 = SPLIT ? 0 : 8;  // B buffer rows, first row of D
   static constexpr uint32_t SBOB = NC * 128, BBYTES = (BROWS / 8) * SBOB;
-  static constexpr int TCOLS = SPLIT ? 64 : 32;                  // tensor-memory columns
+  // tensor-memory columns: per M-block CPB (32, or 64 with an accumulator per direction)
+  static constexpr int CPB = SPLIT ? 64 : 32, TCOLS = CPB * MB;
   // exchange k pitch: F, or F + 4 where F is an odd multiple of 16, so that
   // the k pitch is 4 times an odd number modulo 32 (the stride-XK writes of
   // a warp then spread over the banks)
   static constexpr int XK = F + ((F % 32) == 16 ? 4 : 0), XE = N1 * XK, XF = EPB * XE;
-  static constexpr int LOADS = (TN + 127) / 128;                 // X values per thread and tile
+  static constexpr int LOADS = (TN + THREADS - 1) / THREADS;     // X values per thread and tile
   static constexpr uint32_t OFF_R = 0, OFF_S = ABYTES, OFF_T = 2 * ABYTES, OFF_X0 = 3 * ABYTES,
                             OFF_X1 = OFF_X0 + (uint32_t)(XF * 4 + 15) / 16 * 16,
                             OFF_BD = OFF_X1 + (uint32_t)(XF * 4 + 15) / 16 * 16, OFF_BDT = OFF_BD + BBYTES,
@@ -482,18 +488,19 @@ struct GShape {
   static_assert(ABYTES % 16 == 0 && BBYTES % 16 == 0, "16-byte aligned operand buffers");
 };
 // resident CTAs per SM: as the order-7 kernel up to N1 = 8; above, a thread
-// holds three rows of N1 values, so four CTAs (up to 128 registers)
+// holds three rows of N1 values, so four CTAs of 128 threads or two of 256
+// (up to 128 registers)
 template <int N1, int KIND>
-constexpr int kCtasGen = N1 > 8 ? 4 : kCtasPerSm<KIND>;
+constexpr int kCtasGen = N1 * N1 > 128 ? 2 : (N1 > 8 ? 4 : kCtasPerSm<KIND>);
 
 template <int N1, int KIND, int OP>
-__global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
+__global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND>)
     ax_umma_gen_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
                        const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
                        int *__restrict__ err) {
   using P = fiber::Native<float>;
   using G = GShape<N1, OP>;
-  constexpr int ESZ = G::ESZ, F = G::F, EPB = G::EPB, N3 = G::N3;
+  constexpr int ESZ = G::ESZ, F = G::F, EPB = G::EPB, N3 = G::N3, NT = G::THREADS;
   constexpr int GW = fiber::GeoWords<KIND>::value;
   extern __shared__ __align__(128) unsigned char sm[];
   unsigned char *bufR = sm + G::OFF_R, *bufS = sm + G::OFF_S, *bufT = sm + G::OFF_T;
@@ -508,9 +515,9 @@ __global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
 
   // the three operand buffers zeroed (pads stay zero), then D and D^T in
   // their B buffers (rows a, K = m and rows m, K = a), zero elsewhere
-  for (uint32_t q = tid; q < 3 * G::ABYTES / 16; q += kThreads) ((uint4 *)sm)[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t q = tid; q < 3 * G::ABYTES / 16; q += NT) ((uint4 *)sm)[q] = make_uint4(0u, 0u, 0u, 0u);
   constexpr int KB = G::NC * G::PER;  // K positions per B row
-  for (int q = tid; q < 2 * G::BROWS * KB; q += kThreads) {
+  for (int q = tid; q < 2 * G::BROWS * KB; q += NT) {
     const int which = q / (G::BROWS * KB), row = (q % (G::BROWS * KB)) / KB, k = q % KB, a = row - G::BROW0;
     float v = 0.0f;
     if (a >= 0 && a < N1 && k < N1) v = which == 0 ? Dp[a * N1 + k] : Dp[k * N1 + a];
@@ -531,7 +538,8 @@ __global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+  // TMEM lane 32 (warp % 4) + lane of the thread's M-block (tid / 128), whose columns start at CPB (tid / 128)
+  const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(G::CPB * (tid >> 7));
   const uint32_t aR = smem_u32(bufR), aS = smem_u32(bufS), aT = smem_u32(bufT);
   const uint32_t aBD = smem_u32(sm + G::OFF_BD), aBDT = smem_u32(sm + G::OFF_BDT);
   const int la = tid % N1, lb = (tid / N1) % N1, le = tid / F;
@@ -542,18 +550,22 @@ __global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
   // the six (forward or transposed) contractions of a tile, issued by one thread
   auto issue = [&](uint32_t aB) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if constexpr (!G::SPLIT) {
-      mma<OP>(tmem, desc(aR, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
-      mma<OP>(tmem, desc(aS, G::LBO, G::SBO), desc(aB, G::LBO, G::SBOB), 1u);
-      mma<OP>(tmem + 16, desc(aT, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
-    } else {
-      const uint32_t aA[3] = {aR, aS, aT};
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
+    for (int mb = 0; mb < G::MB; ++mb) {
+      const uint32_t ta = tmem + (uint32_t)(G::CPB * mb), ra = (uint32_t)(mb * 16) * G::SBO;  // 128 rows down
+      if constexpr (!G::SPLIT) {
+        mma<OP>(ta, desc(aR + ra, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
+        mma<OP>(ta, desc(aS + ra, G::LBO, G::SBO), desc(aB, G::LBO, G::SBOB), 1u);
+        mma<OP>(ta + 16, desc(aT + ra, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
+      } else {
+        const uint32_t aA[3] = {aR + ra, aS + ra, aT + ra};
 #pragma unroll
-        for (int q = 0; q < G::NI; ++q)
-          mma<OP>(tmem + 16 * d, desc(aA[d] + q * kStepA, G::LBO, G::SBO), desc(aB + q * kStepA, G::LBO, G::SBOB),
-                  q > 0 ? 1u : 0u);
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int q = 0; q < G::NI; ++q)
+            mma<OP>(ta + 16 * d, desc(aA[d] + q * kStepA, G::LBO, G::SBO), desc(aB + q * kStepA, G::LBO, G::SBOB),
+                    q > 0 ? 1u : 0u);
+      }
     }
     commit(smem_u32(bar));
   };
@@ -604,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
     const int64_t nv = tt < ntile ? ((E - b0) < EPB ? (E - b0) : EPB) * N3 : 0;
 #pragma unroll
     for (int s2 = 0; s2 < G::LOADS; ++s2) {
-      const int m = tid + kThreads * s2;
+      const int m = tid + NT * s2;
       xv[s2] = m < nv ? X[b0 * N3 + m] : 0.0f;
     }
   };
@@ -616,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
     // 1. X into the three operand buffers (zeros beyond the last element)
 #pragma unroll
     for (int s2 = 0; s2 < G::LOADS; ++s2) {
-      const int m = tid + kThreads * s2;
+      const int m = tid + NT * s2;
       if (m < G::TN) {
         const int e = m / N3, rem = m % N3, i = rem % N1, j = (rem / N1) % N1, k = rem / F;
         const uint32_t c = code<OP>(xnext[s2]);
@@ -626,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, kCtasGen<N1, KIND>)
       }
     }
     if constexpr (GW > 0) {
-      for (int m = tid; m < nel * GW; m += kThreads) sgeo[m] = geo[e0 * GW + m];
+      for (int m = tid; m < nel * GW; m += NT) sgeo[m] = geo[e0 * GW + m];
     }
     load_x(t + gridDim.x, xnext);  // the next tile's X, in flight meanwhile
     proxy_fence();
@@ -720,7 +732,7 @@ cudaError_t launch_gen(const AxArgs &a, const float *Dp) {
   }
   const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
   const int64_t grid = ntile < cap ? ntile : cap;
-  ax_umma_gen_kernel<N1, KIND, OP><<<(unsigned)grid, kThreads, G::BYTES, a.stream>>>(
+  ax_umma_gen_kernel<N1, KIND, OP><<<(unsigned)grid, G::THREADS, G::BYTES, a.stream>>>(
       a.E, (const float *)a.geo, (const float *)a.lam, (const float *)a.X, (float *)a.Y, Dp, a.err);
   return cudaGetLastError();
 }
