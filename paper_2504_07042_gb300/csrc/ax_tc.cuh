@@ -1,6 +1,9 @@
 // AxLocal with the six sum-factorised contractions of Algorithm 1 on the
 // tensor cores (mma.sync m16n8k8, operands TF32, BF16 or FP16, accumulation
-// in FP32); X, Y, the geometry and (r,s,t) = G (x0,x1,x2) stay FP32.
+// in FP32); X, Y, the geometry and (r,s,t) = G (x0,x1,x2) stay FP32.  The
+// tcgen05 kernels of ax_umma.cuh run every order by default; this warp-level
+// kernel is the second tile variant (the first for TF32 at N = 11, where it
+// measured faster), which the batch autotuner compares with them.
 //
 // A contraction along direction d maps the element's N1^2 fibers of that
 // direction through D (forward) or D^T (transposed).  Written as a product

@@ -1,7 +1,8 @@
 // AxLocal with the six contractions of Algorithm 1 on the 5th-generation
 // tensor cores (tcgen05.mma kind::tf32 for TF32 operands, kind::f16 for
-// BF16 and FP16 operands; accumulation in tensor memory), for order N = 7
-// (N1 = 8).
+// BF16 and FP16 operands; accumulation in tensor memory): the kernel tuned
+// for order N = 7 (N1 = 8) described first, and below it the same structure
+// sized to every other order (ax_umma_gen_kernel).
 //
 // A contraction along one direction is a [fibers x 8] by [8 x 8] product.
 // Two elements' 64 fibers of one direction make the M = 128 rows of one
