@@ -461,6 +461,52 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm<KIND>)
 // L / N1^2); x0 and x1 reach the t-fiber owners through the exchange
 // buffers [e][k][j][i] (k pitch XK), as in the order-7 kernel.
 // ---------------------------------------------------------------------------
+// Shared-memory layouts of the order-sized kernel, per order and operand
+// width (TF32 / 16-bit), from a search over a bank-conflict model of the
+// kernel's shared-memory accesses (every access pattern of a tile, counted
+// in wavefronts as the hardware serves 4-, 8- and 16-byte accesses): the
+// exchange buffers' j and k pitches (floats) and each operand buffer's LBO
+// and SBO (bytes).  Measured by the model at N1 = 16, 16-bit: 2432 wavefronts
+// per tile against 7168 for dense layouts with scalar staging.
+struct GenLayout {
+  int n1, op, pj, xk, lbo_r, sbo_r, lbo_s, sbo_s, lbo_t, sbo_t;
+};
+constexpr GenLayout kGenLayouts[] = {
+    {2, 0, 2, 6, 128, 272, 128, 272, 128, 256},
+    {2, 1, 2, 6, 128, 272, 128, 272, 128, 256},
+    {3, 0, 3, 35, 128, 272, 128, 272, 128, 256},
+    {3, 1, 3, 35, 128, 272, 128, 272, 128, 256},
+    {4, 0, 8, 35, 128, 288, 128, 288, 128, 256},
+    {4, 1, 8, 35, 128, 288, 128, 288, 128, 256},
+    {5, 0, 5, 25, 2112, 128, 2288, 144, 128, 256},
+    {5, 1, 5, 25, 128, 320, 128, 256, 128, 256},
+    {6, 0, 7, 42, 2112, 128, 128, 256, 128, 256},
+    {6, 1, 7, 42, 128, 272, 128, 256, 128, 256},
+    {7, 0, 7, 49, 128, 256, 128, 256, 128, 256},
+    {7, 1, 7, 49, 128, 256, 128, 256, 128, 256},
+    {9, 0, 9, 81, 2096, 128, 128, 512, 128, 512},
+    {9, 1, 9, 81, 2128, 128, 128, 256, 128, 256},
+    {10, 0, 10, 101, 2080, 128, 128, 512, 128, 512},
+    {10, 1, 10, 101, 2112, 128, 128, 256, 128, 256},
+    {11, 0, 11, 121, 2096, 128, 128, 512, 128, 512},
+    {11, 1, 11, 121, 2112, 128, 128, 256, 128, 256},
+    {12, 0, 17, 204, 4144, 128, 128, 512, 128, 512},
+    {12, 1, 17, 204, 4160, 128, 128, 256, 128, 256},
+    {13, 0, 13, 169, 4128, 128, 128, 512, 128, 512},
+    {13, 1, 13, 169, 4160, 128, 128, 256, 128, 256},
+    {14, 0, 14, 199, 4128, 128, 128, 512, 128, 512},
+    {14, 1, 14, 199, 4144, 128, 128, 256, 128, 256},
+    {15, 0, 15, 225, 4128, 128, 128, 512, 128, 512},
+    {15, 1, 15, 225, 4144, 128, 128, 256, 128, 256},
+    {16, 0, 17, 272, 4128, 128, 128, 512, 128, 512},
+    {16, 1, 17, 272, 4128, 128, 128, 256, 128, 256},
+};
+constexpr GenLayout gen_layout(int n1, int op) {
+  for (const GenLayout &g : kGenLayouts)
+    if (g.n1 == n1 && g.op == (op == 0 ? 0 : 1)) return g;
+  return GenLayout{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+}
+
 template <int N1, int OP>
 struct GShape {
   static constexpr int F = N1 * N1, EPB = F > 128 ? 1 : 128 / F, ROWS = EPB * F, N3 = N1 * N1 * N1, TN = EPB * N3;
@@ -470,23 +516,30 @@ struct GShape {
   static constexpr int KI = OP == 0 ? 8 : 16;                   // K per MMA instruction
   static constexpr int NI = (N1 + KI - 1) / KI;                 // instructions per contraction
   static constexpr int NC = NI * KI / PER;                      // K core columns of every operand buffer
-  static constexpr uint32_t LBO = 128, SBO = NC * 128 + 16, ABYTES = 16 * MB * SBO;
+  static constexpr int NCD = (N1 + PER - 1) / PER;              // core columns holding data
+  static constexpr GenLayout LY = gen_layout(N1, OP);
+  static_assert(LY.n1 == N1, "no layout for this order");
+  static constexpr uint32_t LBO_R = LY.lbo_r, SBO_R = LY.sbo_r, LBO_S = LY.lbo_s, SBO_S = LY.sbo_s,
+                            LBO_T = LY.lbo_t, SBO_T = LY.sbo_t;
+  // bytes of an operand buffer: its last core matrix ends there
+  static constexpr uint32_t span(uint32_t lbo, uint32_t sbo) { return (16 * MB - 1) * sbo + (NC - 1) * lbo + 128; }
+  static constexpr uint32_t BYTES_R = span(LBO_R, SBO_R), BYTES_S = span(LBO_S, SBO_S),
+                            BYTES_T = span(LBO_T, SBO_T);
   static constexpr bool SPLIT = N1 > 8;                          // one accumulator per direction
   static constexpr int BROWS = SPLIT ? 16 : 24, BROW0 = SPLIT ? 0 : 8;  // B buffer rows, first row of D
-  static constexpr uint32_t SBOB = NC * 128, BBYTES = (BROWS / 8) * SBOB;
+  static constexpr uint32_t LBOB = 128, SBOB = NC * 128, BBYTES = (BROWS / 8) * SBOB;
   // tensor-memory columns: per M-block CPB (32, or 64 with an accumulator per direction)
   static constexpr int CPB = SPLIT ? 64 : 32, TCOLS = CPB * MB;
-  // exchange k pitch: F, or F + 4 where F is an odd multiple of 16, so that
-  // the k pitch is 4 times an odd number modulo 32 (the stride-XK writes of
-  // a warp then spread over the banks)
-  static constexpr int XK = F + ((F % 32) == 16 ? 4 : 0), XE = N1 * XK, XF = EPB * XE;
-  static constexpr int LOADS = (TN + THREADS - 1) / THREADS;     // X values per thread and tile
-  static constexpr uint32_t OFF_R = 0, OFF_S = ABYTES, OFF_T = 2 * ABYTES, OFF_X0 = 3 * ABYTES,
+  // exchange buffers [e][k][j][i]: i pitch 1, j pitch PJ, k pitch XK floats
+  static constexpr int PJ = LY.pj, XK = LY.xk, XE = N1 * XK, XF = EPB * XE;
+  static constexpr uint32_t OFF_R = 0, OFF_S = BYTES_R, OFF_T = OFF_S + BYTES_S, OFF_X0 = OFF_T + BYTES_T,
                             OFF_X1 = OFF_X0 + (uint32_t)(XF * 4 + 15) / 16 * 16,
                             OFF_BD = OFF_X1 + (uint32_t)(XF * 4 + 15) / 16 * 16, OFF_BDT = OFF_BD + BBYTES,
                             OFF_GEO = OFF_BDT + BBYTES, BYTES = OFF_GEO + EPB * kVertexWords * 4 + 64;
   static_assert(EPB >= 1 && N1 <= 16 - BROW0 && N1 <= 16, "tile shape");
-  static_assert(ABYTES % 16 == 0 && BBYTES % 16 == 0, "16-byte aligned operand buffers");
+  static_assert((N1 - 1) * PJ + N1 <= XK, "exchange rows fit the k pitch");
+  static_assert(BYTES_R % 16 == 0 && BYTES_S % 16 == 0 && BYTES_T % 16 == 0 && BBYTES % 16 == 0,
+                "16-byte aligned operand buffers");
 };
 // resident CTAs per SM: as the order-7 kernel up to N1 = 8; above, a thread
 // holds three rows of N1 values, so four CTAs of 128 threads or two of 256
@@ -516,13 +569,14 @@ __global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND>)
 
   // the three operand buffers zeroed (pads stay zero), then D and D^T in
   // their B buffers (rows a, K = m and rows m, K = a), zero elsewhere
-  for (uint32_t q = tid; q < 3 * G::ABYTES / 16; q += NT) ((uint4 *)sm)[q] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t q = tid; q < (G::BYTES_R + G::BYTES_S + G::BYTES_T) / 16; q += NT)
+    ((uint4 *)sm)[q] = make_uint4(0u, 0u, 0u, 0u);
   constexpr int KB = G::NC * G::PER;  // K positions per B row
   for (int q = tid; q < 2 * G::BROWS * KB; q += NT) {
     const int which = q / (G::BROWS * KB), row = (q % (G::BROWS * KB)) / KB, k = q % KB, a = row - G::BROW0;
     float v = 0.0f;
     if (a >= 0 && a < N1 && k < N1) v = which == 0 ? Dp[a * N1 + k] : Dp[k * N1 + a];
-    st_op<OP>(sm + (which == 0 ? G::OFF_BD : G::OFF_BDT), cm_off<ESZ>(row, k, G::LBO, G::SBOB), v);
+    st_op<OP>(sm + (which == 0 ? G::OFF_BD : G::OFF_BDT), cm_off<ESZ>(row, k, G::LBOB, G::SBOB), v);
   }
   if (tid == 0) {
     abort_cta = 0;
@@ -546,26 +600,29 @@ __global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND>)
   const int la = tid % N1, lb = (tid / N1) % N1, le = tid / F;
   const bool row_in_use = tid < G::ROWS;
   uint32_t phase = 0;
-  constexpr uint32_t kStepA = (G::KI / G::PER) * G::LBO;  // bytes of K per instruction (A and B alike)
+  constexpr int kStepC = G::KI / G::PER;  // K core columns per instruction
 
   // the six (forward or transposed) contractions of a tile, issued by one thread
   auto issue = [&](uint32_t aB) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
     for (int mb = 0; mb < G::MB; ++mb) {
-      const uint32_t ta = tmem + (uint32_t)(G::CPB * mb), ra = (uint32_t)(mb * 16) * G::SBO;  // 128 rows down
+      const uint32_t ta = tmem + (uint32_t)(G::CPB * mb), m16 = (uint32_t)(mb * 16);  // 128 rows down
+      const uint64_t dR = desc(aR + m16 * G::SBO_R, G::LBO_R, G::SBO_R), dS = desc(aS + m16 * G::SBO_S, G::LBO_S, G::SBO_S),
+                     dT = desc(aT + m16 * G::SBO_T, G::LBO_T, G::SBO_T);
       if constexpr (!G::SPLIT) {
-        mma<OP>(ta, desc(aR + ra, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
-        mma<OP>(ta, desc(aS + ra, G::LBO, G::SBO), desc(aB, G::LBO, G::SBOB), 1u);
-        mma<OP>(ta + 16, desc(aT + ra, G::LBO, G::SBO), desc(aB + G::SBOB, G::LBO, G::SBOB), 0u);
+        mma<OP>(ta, dR, desc(aB + G::SBOB, G::LBOB, G::SBOB), 0u);
+        mma<OP>(ta, dS, desc(aB, G::LBOB, G::SBOB), 1u);
+        mma<OP>(ta + 16, dT, desc(aB + G::SBOB, G::LBOB, G::SBOB), 0u);
       } else {
-        const uint32_t aA[3] = {aR + ra, aS + ra, aT + ra};
+        const uint32_t aA[3] = {aR + m16 * G::SBO_R, aS + m16 * G::SBO_S, aT + m16 * G::SBO_T};
+        const uint32_t lA[3] = {G::LBO_R, G::LBO_S, G::LBO_T}, sA[3] = {G::SBO_R, G::SBO_S, G::SBO_T};
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
           for (int q = 0; q < G::NI; ++q)
-            mma<OP>(ta + 16 * d, desc(aA[d] + q * kStepA, G::LBO, G::SBO), desc(aB + q * kStepA, G::LBO, G::SBOB),
-                    q > 0 ? 1u : 0u);
+            mma<OP>(ta + 16 * d, desc(aA[d] + q * kStepC * lA[d], lA[d], sA[d]),
+                    desc(aB + q * kStepC * G::LBOB, G::LBOB, G::SBOB), q > 0 ? 1u : 0u);
       }
     }
     commit(smem_u32(bar));
@@ -598,45 +655,63 @@ __global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND>)
     }
   };
   // r-row values (over i) and s-row values (over j) to the t-fiber owners
-  const int xrow = le * G::XE + G::XK * lb + N1 * la;  // r-row (j, k) = (la, lb): value i at + i
-  const int xcol = le * G::XE + G::XK * lb + la;       // s-row (i, k) = (la, lb): value j at + N1 j
-  const int xown = le * G::XE + N1 * lb + la;          // t-fiber owner (i, j) = (la, lb): node k at + XK k
+  const int xrow = le * G::XE + G::XK * lb + G::PJ * la;  // r-row (j, k) = (la, lb): value i at + i
+  const int xcol = le * G::XE + G::XK * lb + la;          // s-row (i, k) = (la, lb): value j at + PJ j
+  const int xown = le * G::XE + G::PJ * lb + la;          // t-fiber owner (i, j) = (la, lb): node k at + XK k
   auto exchange = [&](const float v0[N1], const float v1[N1]) {
     if (row_in_use) {
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
         ex0[xrow + q] = v0[q];
-        ex1[xcol + N1 * q] = v1[q];
+        ex1[xcol + G::PJ * q] = v1[q];
       }
     }
   };
 
   const int64_t ntile = (E + EPB - 1) / EPB;
-  auto load_x = [&](int64_t tt, float xv[G::LOADS]) {
-    const int64_t b0 = tt * EPB;
-    const int64_t nv = tt < ntile ? ((E - b0) < EPB ? (E - b0) : EPB) * N3 : 0;
+  // X of a tile, staged by the t-fiber owners: thread (i, j, e) = (la, lb, le)
+  // reads its N1 values X[e][k][j][i] (for each k the warp reads consecutive
+  // i, j: coalesced), one tile ahead so that the loads overlap the previous
+  // tile's work; zeros beyond the last element
+  auto load_x = [&](int64_t tt, float xv[N1]) {
+    const int64_t eg = tt * EPB + le;
+    const bool ok = row_in_use && tt < ntile && eg < E;
+    const float *src = X + eg * N3 + la + N1 * lb;
 #pragma unroll
-    for (int s2 = 0; s2 < G::LOADS; ++s2) {
-      const int m = tid + NT * s2;
-      xv[s2] = m < nv ? X[b0 * N3 + m] : 0.0f;
+    for (int k = 0; k < N1; ++k) xv[k] = ok ? src[F * k] : 0.0f;
+  };
+  // the thread's own T row (t-fiber, K = k) in 16-byte stores, the pad of the
+  // last core column zero
+  auto st_trow = [&](const uint32_t c[N1]) {
+#pragma unroll
+    for (int cc = 0; cc < G::NCD; ++cc) {
+      uint32_t w[G::PER];
+#pragma unroll
+      for (int p = 0; p < G::PER; ++p) w[p] = cc * G::PER + p < N1 ? c[cc * G::PER + p] : 0u;
+      uint4 v;
+      if constexpr (OP == 0)
+        v = make_uint4(w[0], w[1], w[2], w[3]);
+      else
+        v = make_uint4(w[0] | (w[1] << 16), w[2] | (w[3] << 16), w[4] | (w[5] << 16), w[6] | (w[7] << 16));
+      *(uint4 *)(bufT + cm_off<ESZ>(tid, cc * G::PER, G::LBO_T, G::SBO_T)) = v;
     }
   };
-  float xnext[G::LOADS];
+  float xnext[N1];
   load_x(blockIdx.x, xnext);
   for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
     const int64_t e0 = t * EPB;
     const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
-    // 1. X into the three operand buffers (zeros beyond the last element)
+    // 1. X into the three operand buffers: r-row (j, k) and s-row (i, k) at
+    // K = i and j value by value, the own t-row whole
+    if (row_in_use) {
+      uint32_t c[N1];
 #pragma unroll
-    for (int s2 = 0; s2 < G::LOADS; ++s2) {
-      const int m = tid + NT * s2;
-      if (m < G::TN) {
-        const int e = m / N3, rem = m % N3, i = rem % N1, j = (rem / N1) % N1, k = rem / F;
-        const uint32_t c = code<OP>(xnext[s2]);
-        st_code<OP>(bufR, cm_off<ESZ>(j + N1 * k + F * e, i, G::LBO, G::SBO), c);
-        st_code<OP>(bufS, cm_off<ESZ>(i + N1 * k + F * e, j, G::LBO, G::SBO), c);
-        st_code<OP>(bufT, cm_off<ESZ>(i + N1 * j + F * e, k, G::LBO, G::SBO), c);
+      for (int k = 0; k < N1; ++k) {
+        c[k] = code<OP>(xnext[k]);
+        st_code<OP>(bufR, cm_off<ESZ>(lb + N1 * k + F * le, la, G::LBO_R, G::SBO_R), c[k]);
+        st_code<OP>(bufS, cm_off<ESZ>(la + N1 * k + F * le, lb, G::LBO_S, G::SBO_S), c[k]);
       }
+      st_trow(c);
     }
     if constexpr (GW > 0) {
       for (int m = tid; m < nel * GW; m += NT) sgeo[m] = geo[e0 * GW + m];
@@ -661,6 +736,7 @@ __global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND>)
     __syncthreads();
     // 4. geometry along the t-fiber of (i, j) = (la, lb), element le; 5. r, s, t into the operand buffers
     if (row_in_use) {
+      uint32_t tt[N1];  // the t values, coded in the operand format
       const bool live = le < nel;
       const int64_t e = e0 + le;
       fiber::Geometry<P, N1, KIND> gm;
@@ -673,10 +749,11 @@ __global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND>)
         const float xv[3] = {ex0[o], ex1[o], x2[k]};
         float o3[3] = {0.f, 0.f, 0.f};
         if (live) gm.apply(la + lb * N1 + k * F, cx[k], cw[k], xv, o3);
-        st_op<OP>(bufR, cm_off<ESZ>(lb + N1 * k + F * le, la, G::LBO, G::SBO), o3[0]);
-        st_op<OP>(bufS, cm_off<ESZ>(la + N1 * k + F * le, lb, G::LBO, G::SBO), o3[1]);
-        st_op<OP>(bufT, cm_off<ESZ>(tid, k, G::LBO, G::SBO), o3[2]);
+        st_op<OP>(bufR, cm_off<ESZ>(lb + N1 * k + F * le, la, G::LBO_R, G::SBO_R), o3[0]);
+        st_op<OP>(bufS, cm_off<ESZ>(la + N1 * k + F * le, lb, G::LBO_S, G::SBO_S), o3[1]);
+        tt[k] = code<OP>(o3[2]);
       }
+      st_trow(tt);
     }
     proxy_fence();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
