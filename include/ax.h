@@ -63,9 +63,8 @@ typedef enum {
   AX_FP64 = 0,  /* X, Y float64; native FP64 arithmetic */
   AX_FP32 = 1,  /* X, Y float32; FP32 arithmetic */
   AX_TF32 = 2,  /* X, Y float32; the six contractions on tensor cores (tcgen05.mma with tensor-memory
-                   accumulators; mma.sync m16n8k8 at N = 11, where it measured faster) with TF32
-                   operands and FP32 accumulation; geometry and G x in FP32 (error about 1-2 u,
-                   u = 2^-11, against the FP64 result) */
+                   accumulators) with TF32 operands and FP32 accumulation; geometry and G x in FP32
+                   (error about 1-2 u, u = 2^-11, against the FP64 result) */
   AX_BF16 = 3,  /* as AX_TF32 with BF16 operands (u = 2^-8) */
   AX_FP16 = 4,  /* as AX_TF32 with FP16 operands (u = 2^-11; inputs must stay inside FP16's range,
                    which the mixed-precision solver's scaling by ||r||_inf ensures) */

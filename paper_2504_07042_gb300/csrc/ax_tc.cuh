@@ -2,8 +2,8 @@
 // tensor cores (mma.sync m16n8k8, operands TF32, BF16 or FP16, accumulation
 // in FP32); X, Y, the geometry and (r,s,t) = G (x0,x1,x2) stay FP32.  The
 // tcgen05 kernels of ax_umma.cuh run every order by default; this warp-level
-// kernel is the second tile variant (the first for TF32 at N = 11, where it
-// measured faster), which the batch autotuner compares with them.
+// kernel is the second tile variant, which the batch autotuner compares with
+// them.
 //
 // A contraction along direction d maps the element's N1^2 fibers of that
 // direction through D (forward) or D^T (transposed).  Written as a product
@@ -299,13 +299,9 @@ cudaError_t launch_tc_kind(const AxArgs &a, const float *Dp) {
 template <int MODE, int N1>
 cudaError_t launch_tc_n(const AxArgs &a, const float *Dp) {
   if constexpr (N1 >= 2 && N1 != 8) {
-    // every order but 7: the tcgen05 kernel sized to the order.  Tile
-    // variant 0 is the kernel measured faster for the (order, format), 1 the
-    // other: tcgen05 first everywhere but TF32 at N = 11 (144 fibers per
-    // direction fill two 128-row MMA blocks to 56%; measured on GB300 at the
-    // order-sweep size, trilinear: tcgen05 125.7 GDOF/s, mma.sync 134.6)
-    constexpr bool kUmmaFirst = !(N1 == 12 && MODE == kTF32);
-    if ((a.tile != 1) == kUmmaFirst) {
+    // every order but 7: the tcgen05 kernel sized to the order (tile
+    // variant 1 selects the mma.sync kernel below)
+    if (a.tile != 1) {
       switch (a.kind) {
         case AX_GEOM_STORED: return umma::launch_gen<N1, AX_GEOM_STORED, MODE>(a, Dp);
         case AX_GEOM_TRILINEAR: return umma::launch_gen<N1, AX_GEOM_TRILINEAR, MODE>(a, Dp);

@@ -541,14 +541,17 @@ struct GShape {
   static_assert(BYTES_R % 16 == 0 && BYTES_S % 16 == 0 && BYTES_T % 16 == 0 && BBYTES % 16 == 0,
                 "16-byte aligned operand buffers");
 };
-// resident CTAs per SM: as the order-7 kernel up to N1 = 8; above, a thread
-// holds three rows of N1 values, so four CTAs of 128 threads or two of 256
-// (up to 128 registers)
-template <int N1, int KIND>
-constexpr int kCtasGen = N1 * N1 > 128 ? 2 : (N1 > 8 ? 4 : kCtasPerSm<KIND>);
+// resident CTAs per SM: as the order-7 kernel up to N1 = 8; at N1 = 9..11
+// five of 128 threads (up to 102 registers); above, three of 256 threads
+// (85 registers) where their shared memory fits, else two (and two for the
+// stored kind, which spills at 85 registers)
+template <int N1, int KIND, int OP>
+constexpr int kCtasGen =
+    N1 * N1 > 128 ? ((KIND == AX_GEOM_STORED || 3 * (GShape<N1, OP>::BYTES + 1024) > 228 * 1024) ? 2 : 3)
+                  : (N1 > 8 ? 5 : kCtasPerSm<KIND>);
 
 template <int N1, int KIND, int OP>
-__global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND>)
+__global__ void __launch_bounds__(GShape<N1, OP>::THREADS, kCtasGen<N1, KIND, OP>)
     ax_umma_gen_kernel(int64_t E, const float *__restrict__ geo, const float *__restrict__ lam,
                        const float *__restrict__ X, float *__restrict__ Y, const float *__restrict__ Dp,
                        int *__restrict__ err) {
@@ -806,7 +809,7 @@ cudaError_t launch_gen(const AxArgs &a, const float *Dp) {
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    grid_cap = kCtasGen<N1, KIND> * sms;
+    grid_cap = kCtasGen<N1, KIND, OP> * sms;
   }
   const int64_t cap = a.grid > 0 && a.grid < grid_cap ? a.grid : grid_cap;
   const int64_t grid = ntile < cap ? ntile : cap;
