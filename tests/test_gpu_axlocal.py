@@ -305,3 +305,33 @@ def test_tcgen05_full_size_sampled(ax, orc, kind, prec, u):
     Yref, _ = orc.axlocal_vertices(V[idx], X[idx].astype(np.float64), N)
     assert _relerr(Y[idx], Yref) <= 4 * u
     assert np.isfinite(Y).all()
+
+
+@pytest.mark.parametrize("N", [3, 5, 9, 11, 15])
+@pytest.mark.parametrize("kind,prec,u", [("trilinear", "tf32", 2.0 ** -11), ("parallelepiped", "tf32", 2.0 ** -11),
+                                         ("trilinear", "bf16", 2.0 ** -8), ("parallelepiped", "bf16", 2.0 ** -8),
+                                         ("stored", "bf16", 2.0 ** -8), ("partial", "bf16", 2.0 ** -8)])
+def test_tcgen05_sweep_orders_full_size_sampled(ax, orc, N, kind, prec, u):
+    # the order-sized tcgen05 kernel on the sweep workload of each order (about
+    # 64M local nodes, one or two 128-row MMA blocks per tile), in the launch
+    # configuration the benchmark times: 256 sampled elements against the
+    # oracle at the format's tolerance (4 u); no wait ran out
+    ex, ey, ez = inputs.sweep_box(N)
+    V = inputs.parallelepiped_vertices(ex, ey, ez) if kind == "parallelepiped" else \
+        inputs.box_vertices(ex, ey, ez, perturb=0.1, seed=0)
+    E = V.shape[0]
+    X = inputs.element_vectors(E, N, seed=1).astype(np.float32)
+    dev = torch.device("cuda:0")
+    op = ax.Ax(torch.from_numpy(V).to(dev), N, kind, prec)
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.full_like(Xd, float("nan"))
+    op.ax_local(Xd, Yd)
+    op.ax_check()
+    Y = Yd.double().cpu().numpy()
+    op.ax_destroy()
+    del Xd, Yd
+    rng = np.random.default_rng(97)
+    idx = np.concatenate([[0, E - 1], rng.choice(E, 254, replace=False)])
+    Yref, _ = orc.axlocal_vertices(V[idx], X[idx].astype(np.float64), N)
+    assert _relerr(Y[idx], Yref) <= 4 * u
+    assert np.isfinite(Y).all()
