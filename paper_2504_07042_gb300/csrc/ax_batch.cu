@@ -16,9 +16,8 @@
 //     then launched once per iteration (the per-mesh reference runs each
 //     mesh's solve with its own launches).
 // Autotuning picks, per group (order, geometry kind), the tile variant
-// (FP32: elements per CTA; tensor-core precisions: the tcgen05 or the
-// mma.sync kernel) and the grid (one CTA per element block, or a persistent
-// grid of k CTAs per SM) by timing the group's AxLocal.
+// (FP32: elements per CTA) and the grid (one CTA per element block, or a
+// persistent grid of k CTAs per SM) by timing the group's AxLocal.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -616,10 +615,8 @@ ax_status ax_batch_tune(ax_batch *b, int *tiles, int64_t *grids, void *stream) {
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
   cudaError_t (*L)(const AxArgs &) = launcher(b->prec);
-  // tile variants: FP32 one or two element blocks per CTA; tensor-core
-  // precisions the tcgen05 (0) or the mma.sync (1) kernel
-  const bool tc = b->prec == AX_TF32 || b->prec == AX_BF16 || b->prec == AX_FP16;
-  const int max_tile = (b->prec == AX_FP32 || tc) ? 2 : 1;
+  // tile variants: FP32 one or two element blocks per CTA; one elsewhere
+  const int max_tile = (b->prec == AX_FP32) ? 2 : 1;
   const int mults[] = {0, 1, 2, 4, 8};
   for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
     auto &g = b->groups[gi];
