@@ -64,8 +64,6 @@ def test_mixed_matches_oracle(ax, orc, kind, hi_prec, lo_prec):
     # FP64 refinement around an inner CG whose AxLocal contracts in FP32 or on
     # the tensor cores (TF32/BF16/FP16 operands, FP32 accumulation): the
     # refined solution matches the oracle's FP64 solve
-    if kind == "stored" and lo_prec in ("tf32", "bf16", "fp16"):
-        pytest.skip("tensor-core contractions serve the recompute kinds only")
     N, n = 5, 3
     V = inputs.box_vertices(n, n, n)
     gid, ng = inputs.box_global_ids(n, n, n, N)
