@@ -157,3 +157,41 @@ def test_layout_no_worse_than_dense(key):
     dense_layout = (N1, N1 * N1 + (4 if (N1 * N1) % 32 == 16 else 0)) + (128, s.NC * 128 + 16) * 3
     dense = Shape(N1, op, dense_layout)
     assert tile_wavefronts(s) <= tile_wavefronts(dense)
+
+
+def _consts(block):
+    return {k: int(eval(v)) for k, v in re.findall(r"(k\w+) = ([0-9 *]+)[,;]", block)}
+
+
+def _fmt_blocks():
+    text = open(SRC).read()
+    f0 = text[text.index("struct Fmt<0> {"):]
+    f0 = f0[:f0.index("};")]
+    f16 = text[text.index("struct Fmt16 {"):]
+    f16 = f16[:f16.index("};")]
+    return _consts(f0), _consts(f16)
+
+
+@pytest.mark.parametrize("which", ["tf32", "16-bit"])
+def test_order7_layouts_are_sound(which):
+    # the order-7 kernel's hand-tuned operand layouts: 128 rows (16 row
+    # groups) of K = 8 values; TF32 fills two 16-byte K cores, the 16-bit
+    # formats one (its second K half is the first again, LBO = 0, against a
+    # zero second K half of the B buffers)
+    c = _fmt_blocks()[0 if which == "tf32" else 1]
+    esz = 4 if which == "tf32" else 2
+    ncols = 8 * esz // 16  # K cores holding the 8 values of a row
+    for buf in "RST":
+        lbo, sbo, nbytes = c["kLbo" + buf], c["kSbo" + buf], c["kBytes" + buf]
+        assert lbo % 16 == 0 and sbo % 16 == 0 and nbytes % 16 == 0
+        pos = sorted(g * sbo + col * lbo for g in range(16) for col in range(ncols))
+        assert all(q - p >= 128 for p, q in zip(pos, pos[1:]))
+        assert pos[-1] + 128 <= nbytes
+        if ncols == 1:
+            assert lbo == 0  # the MMA's second K half reads the first again
+    # B buffers: 24 rows (3 row groups) of two K cores (TF32) or of one K core
+    # and the zero second K half (16-bit)
+    lbo, sbo, nbytes = c["kLboB"], c["kSboB"], c["kBytesB"]
+    pos = sorted(g * sbo + col * lbo for g in range(3) for col in range(2))
+    assert all(q - p >= 128 for p, q in zip(pos, pos[1:]))
+    assert pos[-1] + 128 <= nbytes
